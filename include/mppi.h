@@ -1,0 +1,252 @@
+/*
+ * mppi.h -- C ABI of libmppi, a GB300 (sm_103a) implementation of one MPPI
+ * solve of the reference-free drone-racing controller of arXiv 2509.14726
+ * ("Rethinking Reference Trajectories in Agile Drone Racing: A Unified
+ * Reference-Free Model-Based Controller via MPPI").
+ *
+ * One solve (Algorithm 1, one pass of the while loop):
+ *   sample   U^m = U* + dU^m, du ~ N(0, Sigma)            Sec. III-B, Eq. 3
+ *   roll out every U^m through the quadrotor model         Sec. III-A, Eq. 2
+ *   score it: gate progress (Eq. 6/7, Sec. IV-A), contouring (Eq. 9) or
+ *             trajectory tracking (Eq. 8, Sec. IV-B)
+ *   weight   w_m = exp(-J_m / lambda) / sum_i exp(-J_i / lambda)   Eq. 4
+ *   update   U* = sum_m w_m U^m; apply u0*; warm start     Eq. 5, Sec. III-B
+ * The problem it solves is the receding-horizon OCP of Eq. 1.
+ *
+ * Conventions.  All structs are plain data; every pointer argument is a
+ * HOST pointer unless its name starts with d_ (device pointer).  Units: SI,
+ * thrust in N, rates in rad/s, world z up, gravity (0, 0, -g).  State
+ * x = [p(3), v(3), q(4, Hamilton, scalar first, body to world), w(3, body)];
+ * input u = [collective thrust, body-rate command (3), progress
+ * acceleration (contouring only)].  Streams are cudaStream_t passed as void*
+ * (NULL = legacy default stream).
+ *
+ * Errors.  Every call returns an mppi_status; nothing throws across the ABI.
+ * mppi_last_error() returns a thread-local message for the last failure.
+ * A handle is not thread-safe: calls on one handle must be serialised by the
+ * caller (different handles may be used from different threads).
+ *
+ * Ownership.  mppi_create deep-copies model, params and track into device
+ * memory owned by the handle; the caller keeps ownership of everything it
+ * passes in.  mppi_destroy releases the handle's device memory.
+ */
+#ifndef MPPI_H_
+#define MPPI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status codes                                                              */
+/* ------------------------------------------------------------------------ */
+typedef enum {
+  MPPI_OK = 0,
+  MPPI_ERR_ARG = 1,          /* invalid argument (null, size, NaN x0, ...) */
+  MPPI_ERR_OOM = 2,          /* device or pinned allocation failed */
+  MPPI_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  MPPI_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+  MPPI_ERR_NOT_ADMITTED = 5, /* serving: request refused by admission */
+  MPPI_WARN_DEGENERATE = 6   /* every cost non-finite: nominal kept */
+} mppi_status;
+
+enum { MPPI_MODEL_CTBR = 0, MPPI_MODEL_ROTOR_RATE = 1 };
+enum { MPPI_OBJ_GATE = 0, MPPI_OBJ_CONTOUR = 1, MPPI_OBJ_TRACK = 2 };
+enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
+/* accumulation of the K-sample weighted update sum (Eq. 5) */
+enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
+enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };
+
+#define MPPI_NX 13
+#define MPPI_NU 5
+#define MPPI_MAX_N 128     /* longest horizon a handle may use */
+#define MPPI_MAX_GATES 64  /* most gates a track may have */
+
+/* Quadrotor model (Eq. 2).  kind selects the input parameterisation; only
+ * MPPI_MODEL_CTBR (collective thrust + body-rate command, body-rate loop
+ * tau = J k_omega (w_cmd - w)) is implemented; ROTOR_RATE is rejected with
+ * MPPI_ERR_ARG. */
+typedef struct {
+  int32_t kind;
+  float mass;         /* kg */
+  float inertia[3];   /* diagonal of J, kg m^2 */
+  float gravity;      /* m/s^2 */
+  float k_omega;      /* body-rate loop gain, 1/s */
+  float drag[3];      /* diagonal of D in Eq. 2 (0 = no drag) */
+  float u_min[5];     /* input box: thrust, w_cmd x3, progress accel */
+  float u_max[5];
+  float omega_max;    /* body-rate bound of the feasibility penalty */
+  float z_floor;      /* altitude floor of the feasibility penalty */
+} mppi_model_t;
+
+/* Sampling, objective and weighting parameters (Eq. 3-9, Table I). */
+typedef struct {
+  int32_t objective;  /* MPPI_OBJ_* */
+  int32_t K;          /* samples (the paper's M) */
+  int32_t N;          /* horizon steps (the paper's K) */
+  float dt;           /* s; also the control period (warm start shifts 1 step) */
+  float lambda;       /* temperature of Eq. 4 */
+  float sigma[5];     /* diagonal of Sigma (Eq. 3) */
+  uint32_t seed;      /* Philox key word 0 */
+  uint32_t drone_id;  /* Philox key word 1 */
+  float w_limit;      /* feasibility penalty weight */
+  float q_near;       /* Q_near of Eq. 7 */
+  float r_near;       /* distance threshold of Q_near, m */
+  int32_t temporal_rule; /* MPPI_RULE_*: gate-pass consistency rule */
+  float q_lag, q_cont;   /* Eq. 9 lag / contouring weights */
+  float q_omega[3];      /* Eq. 9 body-rate weights */
+  float r_dv, r_dthrust; /* Eq. 9 progress-accel and thrust-change weights */
+  float mu;              /* Eq. 9 progress reward */
+  float v_theta_max;     /* Eq. 9 progress-speed bound */
+  float theta_back, theta_ahead; /* window of the path projection, m */
+  float Q[13], QN[13];   /* Eq. 8 state / terminal weights */
+  float R[4];            /* Eq. 8 input weights (about hover thrust) */
+  int32_t noise_dtype;   /* MPPI_NOISE_*: storage of the sampled noise */
+  int32_t accum;         /* MPPI_ACC_* */
+  int32_t block;         /* threads per block of the rollout (0 = 128) */
+  int32_t N_cap;         /* largest N later solves may use (0 = N) */
+  int32_t K_cap;         /* largest K later solves may use (0 = K) */
+} mppi_params_t;
+
+/* Track: waypoints W, arc-length path P_arc and reference tau_ref
+ * (the inputs of Algorithm 1).  Tables are row-major float32, host memory. */
+typedef struct {
+  int32_t n_gates;
+  int32_t closed;        /* 1: gates repeat (laps) */
+  const float* gates;    /* [n_gates][6]: centre x y z, yaw, half width, half height */
+  int32_t S;             /* path nodes, uniform in arc length */
+  float L;               /* path length, m (nodes L/S apart, closed) */
+  const float* path;     /* [S][6]: position, unit tangent (NULL if S == 0) */
+  int32_t T;             /* reference rows (periodic with period T*dt_ref) */
+  float dt_ref;          /* s between reference rows */
+  const float* ref;      /* [T][13]: p v q w (NULL if T == 0) */
+} mppi_track_t;
+
+typedef struct mppi_s* mppi_handle;
+typedef struct mppi_batch_s* mppi_batch;
+
+/* Fills *m / *p with the library defaults for mass 0.85 kg, inertia
+ * diag(0.0025, 0.0025, 0.0043), thrust in [0, 4 m g], rates in [-10, 10]
+ * rad/s, sigma (0.3 m g, 1, 1, 1, 5), lambda 1 and the cost weights listed in
+ * the design notes.  Returns MPPI_ERR_ARG on NULL. */
+int mppi_default_model(mppi_model_t* m);
+int mppi_default_params(mppi_params_t* p, int32_t objective, int32_t K, int32_t N, float dt);
+
+/* Creates a controller for one drone (Eq. 1 problem data: model, weights,
+ * track).  The nominal starts at hover, the gate index at 0, the Philox
+ * iteration at 0.  Must be called with the target device current.
+ * Errors: MPPI_ERR_ARG (bad sizes: K < 1, N < 1 or > MPPI_MAX_N, n_gates < 1
+ * or > MPPI_MAX_GATES for the gate objective, missing path / reference table
+ * for the contouring / tracking objective), MPPI_ERR_OOM, MPPI_ERR_CUDA. */
+int mppi_create(const mppi_model_t* model, const mppi_params_t* params,
+                const mppi_track_t* track, mppi_handle* out);
+int mppi_destroy(mppi_handle h);
+
+/* One MPPI solve (Algorithm 1 body) from state x0 at time t0 (t0 selects the
+ * tracking reference window; unused otherwise).  Enqueues the kernels on
+ * `stream`, copies u0* (5 floats; the 5th is the progress acceleration for
+ * contouring, 0 otherwise) to u0_out and waits only for that copy.  The
+ * handle's nominal, gate index and RNG counter are updated on the device.
+ * Returns MPPI_WARN_DEGENERATE (u0 = previous nominal) if every cost was
+ * non-finite. */
+int mppi_solve(mppi_handle h, const float x0[13], double t0, void* stream, float u0_out[5]);
+
+/* Same solve with device-resident x0 and u0 (d_x0: 13 floats, d_u0: 5
+ * floats), fully asynchronous: nothing is waited for. */
+int mppi_solve_async(mppi_handle h, const float* d_x0, double t0, void* stream, float* d_u0);
+
+/* Solves n independent drones in one launch sequence (uneven K, N and
+ * objectives allowed).  x0s: [n][13], t0s: [n], u0s_out: [n][5], host.
+ * The first call with a given handle list builds a plan (tile table, CUDA
+ * graph); later calls with the same list reuse it.  Each handle's result is
+ * the one mppi_solve would give (the per-solve reduction order does not
+ * depend on the batch). */
+int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const double* t0s,
+                     void* stream, float* u0s_out);
+
+/* Explicit batch plans (what mppi_solve_batch caches internally).
+ * use_graph = 1 captures the launch sequence in a CUDA graph. */
+int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_batch* out);
+int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* stream, float* u0s_out);
+/* device-side form: d_x0s [n][13], d_t0s [n], d_u0s [n][5]; asynchronous */
+int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s, void* stream,
+                           float* d_u0s);
+int mppi_batch_destroy(mppi_batch b);
+
+/* Changes K and/or N of an existing handle (within K_cap / N_cap).  The
+ * nominal keeps its first rows (the last row repeats when N grows). */
+int mppi_set_shape(mppi_handle h, int32_t K, int32_t N);
+
+/* ---------------- state access (checkpoint / resume, diagnostics) -------- */
+
+/* Nominal U* (after the shift) [N][5]. */
+int mppi_get_nominal(mppi_handle h, float* U);
+/* Weighted average of the last solve before the shift (Eq. 5) [N][5]. */
+int mppi_get_unew(mppi_handle h, float* U);
+/* Per-sample cost of the last solve [K] (double: J is accumulated in
+ * compensated float32 and exported as hi + lo). */
+int mppi_get_costs(mppi_handle h, double* J);
+/* Per-sample gate-progress diagnostics of the last solve: gates passed
+ * inside the horizon and step of the first accepted pass (-1: none). */
+int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass);
+/* Sampled standard normals of the last solve [N][K][5] (the 5th column is
+ * only filled for contouring; BF16 storage is widened to float). */
+int mppi_get_noise(mppi_handle h, float* Z);
+/* Gates passed by each state of the last nominal rollout [N+1]. */
+int mppi_get_passcnt(mppi_handle h, int32_t* passcnt);
+/* Scalars of the last solve: [0] gate index at its start, [1] status,
+ * [2] Philox iteration now, [3] gate index now. */
+int mppi_get_info(mppi_handle h, int32_t info[4]);
+/* theta0, v_theta0 used by the last contouring solve; J_min and the
+ * normaliser sum of Eq. 4 (relative to J_min). */
+int mppi_get_solve_scalars(mppi_handle h, double out[4]);
+/* Tracking reference window of the last solve [N+1][13]. */
+int mppi_get_xref(mppi_handle h, float* xref);
+
+/* Serialises the handle's resident controller state (nominal, RNG
+ * iteration, gate index, pass counts, previous x0, progress state, last
+ * thrust).  With buf == NULL, *size receives the byte count. */
+int mppi_export_state(mppi_handle h, void* buf, size_t* size);
+int mppi_import_state(mppi_handle h, const void* buf, size_t size);
+int mppi_set_gate_index(mppi_handle h, int32_t gate);
+
+/* Uses caller-provided standard normals for the next solve instead of
+ * Philox: d_Z is [N][K][4] float32 (or bf16 when the handle stores BF16
+ * noise) plus, for contouring, d_Z5 [N][K] of the same type.  Device
+ * pointers; the data is copied on `stream` before this returns. */
+int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11), run on the device with the same
+ * round function the noise kernel uses: for i < n, writes the four words of
+ * philox(ctr = (c0 + i, c1, c2, c3), key = (k0, k1)) to d_out[4 i ..].
+ * For testing the generator; d_out is a device buffer of 4 n words. */
+int mppi_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                int32_t n, uint32_t* d_out, void* stream);
+/* Box-Muller normals from the same stream: for i < n, four normals of
+ * (sample i, step k, iteration it, block blk) with key (seed, drone). */
+int mppi_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int32_t n,
+                 float* d_out, void* stream);
+
+/* Rolls out caller-given sequences with the kernel's model and RK4 step:
+ * d_x0 [13], d_U [B][N][4] -> d_X [B][N+1][13].  For model tests. */
+int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B,
+                        const float* d_x0, const float* d_U, float* d_X, void* stream);
+
+/* Device memory the handle holds, bytes. */
+int mppi_device_bytes(mppi_handle h, size_t* bytes);
+/* Device memory a handle with these params would hold, bytes. */
+int mppi_estimate_bytes(const mppi_params_t* params, const mppi_track_t* track, size_t* bytes);
+
+/* Number of kernels the library has launched since load (all entry points). */
+uint64_t mppi_kernel_launches(void);
+
+const char* mppi_last_error(void);
+const char* mppi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPPI_H_ */

@@ -1,0 +1,69 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one slip in a copy of the oracle source (on the CPU),
+compiles it to a temporary library and runs the pin tests against it: at
+least one pin must fail.  This checks the pins, not the CUDA path.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mppi_oracle.c")
+
+MUTATIONS = [
+    ("philox round: high words swapped",
+     "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;"),
+    ("uniform offset 1/2 instead of 1",
+     "((double)(x >> 8) + 1.0)", "((double)(x >> 8) + 0.5)"),
+    ("box-muller cos/sin swapped",
+     "z[0] = r * cos(two_pi * ub);", "z[0] = r * sin(two_pi * ub);"),
+    ("rotation matrix transposed (one entry)",
+     "R[2] = 2 * (x * z + w * y);", "R[2] = 2 * (x * z - w * y);"),
+    ("quaternion product sign",
+     "dx[7] = 0.5 * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);",
+     "dx[7] = 0.5 * (q[0] * w[0] - q[2] * w[2] + q[3] * w[1]);"),
+    ("gyroscopic term sign",
+     "dx[10 + i] = (tau - cx[i]) / Jd[i];", "dx[10 + i] = (tau + cx[i]) / Jd[i];"),
+    ("drag applied in the world frame",
+     "for (int i = 0; i < 3; ++i) DRtv[i] = md->drag[i] * Rtv[i];",
+     "for (int i = 0; i < 3; ++i) DRtv[i] = md->drag[i] * v[i];"),
+    ("RK4 weights 1-1-1-1",
+     "(k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i])", "(1.5 * k1[i] + 1.5 * k2[i] + 1.5 * k3[i] + 1.5 * k4[i])"),
+    ("near-gate term on p_{k+1}",
+     "double d0 = sqrt(dist2(x, g0));", "double d0 = sqrt(dist2(xn, g0));"),
+    ("temporal rule off by one step",
+     "prev_at(cx, k) <= passed", "prev_at(cx, k + 1) <= passed"),
+    ("crossing accepted on s = 0 at the start",
+     "if (!(sa < 0.0 && sb >= 0.0)) return 0;", "if (!(sa <= 0.0 && sb >= 0.0)) return 0;"),
+    ("lag and contouring weights swapped",
+     "double lag = pr->q_lag *", "double lag = pr->q_cont *"),
+    ("terminal tracking weight Q instead of Q_N",
+     "stage += track_err(xn, cx->xref + 13 * N, pr->QN);", "stage += track_err(xn, cx->xref + 13 * N, pr->Q);"),
+    ("temperature multiplies instead of divides",
+     "w[m] = isfinite(J[m]) ? exp(-(J[m] - Jmin) / pr->lambda) : 0.0;",
+     "w[m] = isfinite(J[m]) ? exp(-(J[m] - Jmin) * pr->lambda) : 0.0;"),
+    ("warm start without the shift",
+     "int32_t src = k + 1 < N ? k + 1 : N - 1;", "int32_t src = k;"),
+    ("samples not clamped",
+     "u[j] = clampd(Unom[OR_NU * k + j] + pr->sigma[j] * z[j], md->u_min[j], md->u_max[j]);",
+     "u[j] = Unom[OR_NU * k + j] + pr->sigma[j] * z[j];"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor must appear exactly once"
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so),
+                           str(mut), "-lm"])
+    env = dict(os.environ, MPPI_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
