@@ -240,6 +240,10 @@ int mppi_device_bytes(mppi_handle h, size_t* bytes);
 /* Device memory a handle with these params would hold, bytes. */
 int mppi_estimate_bytes(const mppi_params_t* params, const mppi_track_t* track, size_t* bytes);
 
+/* sizeof(mppi_model_t), sizeof(mppi_params_t), sizeof(mppi_track_t) as
+ * compiled into the library, for binding checks.  Touches no device. */
+int mppi_abi_sizes(size_t out[3]);
+
 /* Number of kernels the library has launched since load (all entry points). */
 uint64_t mppi_kernel_launches(void);
 

@@ -1,0 +1,1000 @@
+// mppi_api.cu -- host side of the libmppi C ABI (see include/mppi.h).
+//
+// A handle owns one device slab: its solve descriptor, the resident controller
+// state (nominal U*, Philox iteration, gate index, pass counts, previous x0,
+// progress state) and the per-solve buffers (noise, costs, tile partials).
+// Solves enqueue the kernels of mppi_kernels.cu on the caller's stream; u0 is
+// written by the device into mapped pinned host memory, so a synchronous solve
+// waits for one event and copies nothing.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mppi_device.cuh"
+#include "mppi_launch.h"
+
+using namespace mppi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) return fail(MPPI_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Slab {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = al256(off + bytes);
+    return o;
+  }
+};
+
+// pinned host memory the device writes u0 / status into
+struct HostIO {
+  float* u0 = nullptr;      // [n][5]
+  int32_t* status = nullptr;
+  float* x0 = nullptr;      // [n][13]
+  double* t0 = nullptr;     // [n]
+  float* d_u0 = nullptr;    // device aliases of the mapped buffers
+  int32_t* d_status = nullptr;
+  float* d_x0 = nullptr;
+  double* d_t0 = nullptr;
+  void* base = nullptr;
+  int n = 0;
+};
+
+int hostio_alloc(HostIO& io, int n) {
+  size_t bytes = al256(sizeof(float) * 5 * n) + al256(sizeof(int32_t) * n) + al256(sizeof(float) * 13 * n) +
+                 al256(sizeof(double) * n);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+    return fail(MPPI_ERR_OOM, "cudaHostAlloc of %zu bytes failed", bytes);
+  memset(p, 0, bytes);
+  char* c = static_cast<char*>(p);
+  io.base = p;
+  io.n = n;
+  io.u0 = reinterpret_cast<float*>(c);
+  c += al256(sizeof(float) * 5 * n);
+  io.status = reinterpret_cast<int32_t*>(c);
+  c += al256(sizeof(int32_t) * n);
+  io.x0 = reinterpret_cast<float*>(c);
+  c += al256(sizeof(float) * 13 * n);
+  io.t0 = reinterpret_cast<double*>(c);
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) return fail(MPPI_ERR_CUDA, "cudaHostGetDevicePointer failed");
+  char* dc = static_cast<char*>(d);
+  io.d_u0 = reinterpret_cast<float*>(dc);
+  dc += al256(sizeof(float) * 5 * n);
+  io.d_status = reinterpret_cast<int32_t*>(dc);
+  dc += al256(sizeof(int32_t) * n);
+  io.d_x0 = reinterpret_cast<float*>(dc);
+  dc += al256(sizeof(float) * 13 * n);
+  io.d_t0 = reinterpret_cast<double*>(dc);
+  return MPPI_OK;
+}
+
+void hostio_free(HostIO& io) {
+  if (io.base) cudaFreeHost(io.base);
+  io = HostIO{};
+}
+
+}  // namespace
+
+struct mppi_s {
+  mppi_model_t model;
+  mppi_params_t params;
+  int device = 0;
+  int K_cap = 0, N_cap = 0, T_cap = 0, nu = 4, block = 128;
+  int n_gates = 0, S = 0, T = 0;
+  unsigned version = 1;
+  SolveDesc hd;          // host copy of the descriptor
+  SolveDesc* d_desc = nullptr;
+  Tile* d_tiles = nullptr;
+  int32_t* d_which = nullptr;  // [1] = 0 (nominal kernel work list)
+  void* slab = nullptr;
+  size_t slab_bytes = 0;
+  HostIO io;
+  cudaEvent_t ev_u0 = nullptr;
+  bool ext_noise_pending = false;
+};
+
+struct mppi_batch_s;
+static std::mutex g_plan_mu;
+static std::vector<mppi_batch_s*> g_plans;
+
+struct mppi_batch_s {
+  std::vector<mppi_handle> hs;
+  std::vector<unsigned> versions;
+  int n = 0;
+  SolveDesc* d_descs = nullptr;
+  struct Group {
+    int objective, bf16, block;
+    uint32_t smem;
+    int n_tiles;
+    Tile* d_tiles;
+  };
+  std::vector<Group> rollout_groups;
+  struct NGroup {
+    int bf16, block, n_tiles;
+    Tile* d_tiles;
+  };
+  std::vector<NGroup> noise_groups;
+  int32_t* d_which = nullptr;
+  int n_which = 0;
+  void* dev = nullptr;
+  HostIO io;
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* t) {
+  if (!m || !p || !t) return fail(MPPI_ERR_ARG, "null model, params or track");
+  if (m->kind != MPPI_MODEL_CTBR)
+    return fail(MPPI_ERR_ARG, "model kind %d not implemented (only collective thrust + body rate)", m->kind);
+  if (!(m->mass > 0) || !(m->inertia[0] > 0) || !(m->inertia[1] > 0) || !(m->inertia[2] > 0))
+    return fail(MPPI_ERR_ARG, "mass and inertia must be positive");
+  if (p->K < 1 || p->N < 1 || p->N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K=%d N=%d out of range", p->K, p->N);
+  if (p->K_cap && p->K_cap < p->K) return fail(MPPI_ERR_ARG, "K_cap < K");
+  if (p->N_cap && (p->N_cap < p->N || p->N_cap > MPPI_MAX_N)) return fail(MPPI_ERR_ARG, "N_cap out of range");
+  if (!(p->dt > 0) || !(p->lambda > 0)) return fail(MPPI_ERR_ARG, "dt and lambda must be positive");
+  if (p->objective < 0 || p->objective > 2) return fail(MPPI_ERR_ARG, "unknown objective %d", p->objective);
+  if (p->noise_dtype != MPPI_NOISE_F32 && p->noise_dtype != MPPI_NOISE_BF16)
+    return fail(MPPI_ERR_ARG, "unknown noise dtype");
+  if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
+  int blk = p->block ? p->block : 128;
+  if (blk < 32 || blk > kMaxBlock || blk % 32) return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, 512]", blk);
+  if (t->n_gates < 0 || t->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
+  if (p->objective == MPPI_OBJ_GATE && (t->n_gates < 1 || !t->gates))
+    return fail(MPPI_ERR_ARG, "gate objective needs at least one gate");
+  if (p->objective == MPPI_OBJ_CONTOUR && (t->S < 2 || !t->path || !(t->L > 0)))
+    return fail(MPPI_ERR_ARG, "contouring needs a path table (S >= 2, L > 0)");
+  if (p->objective == MPPI_OBJ_TRACK && (t->T < 2 || !t->ref || !(t->dt_ref > 0)))
+    return fail(MPPI_ERR_ARG, "tracking needs a reference table (T >= 2, dt_ref > 0)");
+  return MPPI_OK;
+}
+
+struct Sizes {
+  size_t off_desc, off_st, off_U, off_prev, off_gates, off_path, off_ref, off_Z, off_Z5, off_J, off_info, off_pm,
+      off_pS, off_pP, off_ticket, off_unew, off_passcnt, off_xref, total;
+};
+
+Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
+  const int K_cap = p->K_cap ? p->K_cap : p->K;
+  const int N_cap = p->N_cap ? p->N_cap : p->N;
+  const int blk = p->block ? p->block : 128;
+  const int T_cap = (K_cap + blk - 1) / blk;
+  int sq = 1;
+  while (sq * sq < T_cap) ++sq;
+  const int Gn = 2 * sq + 16;  // >= n_groups_for(T) for every T <= T_cap
+  const bool bf16 = p->noise_dtype == MPPI_NOISE_BF16;
+  const bool five = p->objective == MPPI_OBJ_CONTOUR;
+  Slab s;
+  Sizes z;
+  z.off_desc = s.take(sizeof(SolveDesc));
+  z.off_st = s.take(sizeof(DevState));
+  z.off_U = s.take(sizeof(float) * (N_cap * kNU + 8));
+  z.off_prev = s.take(sizeof(int32_t) * (N_cap + 8));
+  z.off_gates = s.take(sizeof(float) * 6 * std::max(1, t->n_gates));
+  z.off_path = s.take(sizeof(float) * 6 * std::max(1, t->S) + 64);
+  z.off_ref = s.take(sizeof(float) * 13 * std::max(1, t->T));
+  z.off_Z = s.take((size_t)N_cap * K_cap * (bf16 ? 8 : 16));
+  z.off_Z5 = s.take(five ? (size_t)N_cap * K_cap * (bf16 ? 2 : 4) : 16);
+  z.off_J = s.take(sizeof(double) * K_cap);
+  z.off_info = s.take(sizeof(int32_t) * K_cap);
+  z.off_pm = s.take(sizeof(double) * (T_cap + Gn + 1));
+  z.off_pS = s.take(sizeof(double) * (T_cap + Gn + 1));
+  z.off_pP = s.take(sizeof(double) * (size_t)(T_cap + Gn + 1) * N_cap * kNU);
+  z.off_ticket = s.take(sizeof(uint32_t) * (Gn + 2));
+  z.off_unew = s.take(sizeof(float) * N_cap * kNU);
+  z.off_passcnt = s.take(sizeof(int32_t) * (N_cap + 1));
+  z.off_xref = s.take(sizeof(float) * 13 * (N_cap + 1));
+  z.total = s.off;
+  return z;
+}
+
+void fill_desc(mppi_handle h) {
+  const mppi_model_t& m = h->model;
+  const mppi_params_t& p = h->params;
+  SolveDesc& d = h->hd;
+  d.mass = m.mass;
+  d.inv_mass = (float)(1.0 / (double)m.mass);
+  d.gravity = m.gravity;
+  d.k_omega = m.k_omega;
+  const double Jx = m.inertia[0], Jy = m.inertia[1], Jz = m.inertia[2];
+  d.gyro[0] = (float)((Jz - Jy) / Jx);
+  d.gyro[1] = (float)((Jx - Jz) / Jy);
+  d.gyro[2] = (float)((Jy - Jx) / Jz);
+  for (int i = 0; i < 3; ++i) d.drag[i] = m.drag[i];
+  d.has_drag = (m.drag[0] != 0.f || m.drag[1] != 0.f || m.drag[2] != 0.f) ? 1 : 0;
+  for (int i = 0; i < kNU; ++i) {
+    d.u_min[i] = m.u_min[i];
+    d.u_max[i] = m.u_max[i];
+    d.sigma[i] = p.sigma[i];
+  }
+  d.omega_max = m.omega_max;
+  d.z_floor = m.z_floor;
+  d.objective = p.objective;
+  d.K = p.K;
+  d.N = p.N;
+  d.nu = h->nu;
+  d.dt = p.dt;
+  d.lambda = p.lambda;
+  d.inv_lambda = (float)(1.0 / (double)p.lambda);
+  d.seed = p.seed;
+  d.drone_id = p.drone_id;
+  d.noise_bf16 = p.noise_dtype == MPPI_NOISE_BF16;
+  d.accum = p.accum;
+  d.w_limit = p.w_limit;
+  d.q_near = p.q_near;
+  d.r_near2 = p.r_near * p.r_near;
+  d.temporal_rule = p.temporal_rule;
+  d.q_lag = p.q_lag;
+  d.q_cont = p.q_cont;
+  for (int i = 0; i < 3; ++i) d.q_omega[i] = p.q_omega[i];
+  d.r_dv = p.r_dv;
+  d.r_dthrust = p.r_dthrust;
+  d.mu = p.mu;
+  d.v_theta_max = p.v_theta_max;
+  d.theta_back = p.theta_back;
+  d.theta_ahead = p.theta_ahead;
+  for (int i = 0; i < kNX; ++i) {
+    d.Q[i] = p.Q[i];
+    d.QN[i] = p.QN[i];
+  }
+  for (int i = 0; i < 4; ++i) d.R[i] = p.R[i];
+  d.hover = m.mass * m.gravity;
+  d.N_cap = h->N_cap;
+  d.block = h->block;
+  d.n_tiles = (p.K + h->block - 1) / h->block;
+  d.ext_noise = 0;
+}
+
+int upload_tiles(mppi_handle h) {
+  const int T = h->hd.n_tiles;
+  std::vector<Tile> tl(T);
+  for (int i = 0; i < T; ++i) tl[i] = Tile{0, i * h->block};
+  CU(cudaMemcpy(h->d_tiles, tl.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice));
+  return MPPI_OK;
+}
+
+void fill_hover(const mppi_handle h, std::vector<float>& U) {
+  U.assign((size_t)h->N_cap * kNU + 8, 0.f);
+  for (int k = 0; k < h->N_cap; ++k) U[(size_t)k * kNU] = h->model.mass * h->model.gravity;
+}
+
+uint32_t merge_cap(int n_tiles) { return (uint32_t)std::max(n_tiles, 32); }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* mppi_last_error(void) { return g_err.c_str(); }
+const char* mppi_version(void) { return "libmppi 1.0 (sm_103a)"; }
+uint64_t mppi_kernel_launches(void) { return (uint64_t)launches_so_far(); }
+
+int mppi_abi_sizes(size_t out[3]) {
+  if (!out) return fail(MPPI_ERR_ARG, "null argument");
+  out[0] = sizeof(mppi_model_t);
+  out[1] = sizeof(mppi_params_t);
+  out[2] = sizeof(mppi_track_t);
+  return MPPI_OK;
+}
+
+int mppi_default_model(mppi_model_t* m) {
+  if (!m) return fail(MPPI_ERR_ARG, "null model");
+  memset(m, 0, sizeof *m);
+  m->kind = MPPI_MODEL_CTBR;
+  m->mass = 0.85f;
+  m->inertia[0] = 0.0025f;
+  m->inertia[1] = 0.0025f;
+  m->inertia[2] = 0.0043f;
+  m->gravity = 9.81f;
+  m->k_omega = 20.f;
+  const float lo[5] = {0.f, -10.f, -10.f, -10.f, -20.f};
+  const float hi[5] = {(float)(4.0 * 0.85 * 9.81), 10.f, 10.f, 10.f, 20.f};
+  for (int i = 0; i < 5; ++i) {
+    m->u_min[i] = lo[i];
+    m->u_max[i] = hi[i];
+  }
+  m->omega_max = 10.f;
+  m->z_floor = 0.f;
+  return MPPI_OK;
+}
+
+int mppi_default_params(mppi_params_t* p, int32_t objective, int32_t K, int32_t N, float dt) {
+  if (!p) return fail(MPPI_ERR_ARG, "null params");
+  memset(p, 0, sizeof *p);
+  p->objective = objective;
+  p->K = K;
+  p->N = N;
+  p->dt = dt;
+  p->lambda = 1.f;
+  const float sg[5] = {(float)(0.3 * 0.85 * 9.81), 1.f, 1.f, 1.f, 5.f};
+  for (int i = 0; i < 5; ++i) p->sigma[i] = sg[i];
+  p->w_limit = 1000.f;
+  p->q_near = 0.3f;
+  p->r_near = 1.5f;
+  p->temporal_rule = MPPI_RULE_TIME_ALIGNED;
+  p->q_lag = 10.f;
+  p->q_cont = 100.f;
+  for (int i = 0; i < 3; ++i) p->q_omega[i] = 0.01f;
+  p->r_dv = 0.01f;
+  p->r_dthrust = 0.01f;
+  p->mu = 1.f;
+  p->v_theta_max = 20.f;
+  p->theta_back = 2.f;
+  p->theta_ahead = 10.f;
+  for (int i = 0; i < 13; ++i) {
+    const float q = i < 3 ? 100.f : i < 6 ? 1.f : i < 10 ? 10.f : 0.1f;
+    p->Q[i] = q;
+    p->QN[i] = 2.f * q;
+  }
+  p->R[0] = 0.01f;
+  p->R[1] = p->R[2] = p->R[3] = 0.1f;
+  p->noise_dtype = MPPI_NOISE_F32;
+  p->accum = MPPI_ACC_KAHAN32;
+  p->block = 128;
+  return MPPI_OK;
+}
+
+int mppi_estimate_bytes(const mppi_params_t* params, const mppi_track_t* track, size_t* bytes) {
+  if (!params || !track || !bytes) return fail(MPPI_ERR_ARG, "null argument");
+  *bytes = plan_sizes(params, track).total;
+  return MPPI_OK;
+}
+
+int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mppi_track_t* track,
+                mppi_handle* out) {
+  if (!out) return fail(MPPI_ERR_ARG, "null output handle");
+  *out = nullptr;
+  int rc = validate(model, params, track);
+  if (rc) return rc;
+  {
+    static std::mutex mu;
+    static std::vector<int> configured;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(configured.begin(), configured.end(), dev) == configured.end()) {
+      CU(configure_kernels());
+      configured.push_back(dev);
+    }
+  }
+  mppi_handle h = new mppi_s();
+  h->model = *model;
+  h->params = *params;
+  CU(cudaGetDevice(&h->device));
+  h->block = params->block ? params->block : 128;
+  h->params.block = h->block;
+  h->K_cap = params->K_cap ? params->K_cap : params->K;
+  h->N_cap = params->N_cap ? params->N_cap : params->N;
+  h->T_cap = (h->K_cap + h->block - 1) / h->block;
+  h->nu = params->objective == MPPI_OBJ_CONTOUR ? 5 : 4;
+  h->n_gates = track->n_gates;
+  h->S = track->S;
+  h->T = track->T;
+  const Sizes z = plan_sizes(&h->params, track);
+  h->slab_bytes = z.total;
+  if (cudaMalloc(&h->slab, z.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(MPPI_ERR_OOM, "cudaMalloc of %zu bytes failed", z.total);
+  }
+  char* b = static_cast<char*>(h->slab);
+  if (cudaMemset(h->slab, 0, z.total) != cudaSuccess) {
+    mppi_destroy(h);
+    return fail(MPPI_ERR_CUDA, "cudaMemset failed");
+  }
+  fill_desc(h);
+  SolveDesc& d = h->hd;
+  h->d_desc = reinterpret_cast<SolveDesc*>(b + z.off_desc);
+  d.st = reinterpret_cast<DevState*>(b + z.off_st);
+  d.U = reinterpret_cast<float*>(b + z.off_U);
+  d.prevcnt = reinterpret_cast<int32_t*>(b + z.off_prev);
+  d.gates = reinterpret_cast<float*>(b + z.off_gates);
+  d.n_gates = track->n_gates;
+  d.closed = track->closed ? 1 : 0;
+  d.path = reinterpret_cast<float*>(b + z.off_path);
+  d.S = track->S;
+  d.L = track->L;
+  d.ds = track->S > 0 ? (float)((double)track->L / track->S) : 1.f;
+  d.inv_ds = track->S > 0 ? (float)((double)track->S / track->L) : 1.f;
+  d.ref = reinterpret_cast<float*>(b + z.off_ref);
+  d.T = track->T;
+  d.dt_ref = track->dt_ref;
+  const bool bf16 = d.noise_bf16;
+  d.Z4 = bf16 ? nullptr : reinterpret_cast<float4*>(b + z.off_Z);
+  d.Zb = bf16 ? reinterpret_cast<uint2*>(b + z.off_Z) : nullptr;
+  d.Z5 = (!bf16 && h->nu == 5) ? reinterpret_cast<float*>(b + z.off_Z5) : nullptr;
+  d.Z5b = (bf16 && h->nu == 5) ? reinterpret_cast<__nv_bfloat16*>(b + z.off_Z5) : nullptr;
+  d.J = reinterpret_cast<double*>(b + z.off_J);
+  d.info = reinterpret_cast<int32_t*>(b + z.off_info);
+  d.part_m = reinterpret_cast<double*>(b + z.off_pm);
+  d.part_S = reinterpret_cast<double*>(b + z.off_pS);
+  d.part_P = reinterpret_cast<double*>(b + z.off_pP);
+  d.ticket = reinterpret_cast<uint32_t*>(b + z.off_ticket);
+  d.unew = reinterpret_cast<float*>(b + z.off_unew);
+  d.passcnt = reinterpret_cast<int32_t*>(b + z.off_passcnt);
+  d.xref = reinterpret_cast<float*>(b + z.off_xref);
+
+  auto cleanup = [&](int code) {
+    mppi_destroy(h);
+    return code;
+  };
+  // track tables
+  if (track->n_gates > 0 && track->gates &&
+      cudaMemcpy((void*)d.gates, track->gates, sizeof(float) * 6 * track->n_gates, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of gates failed"));
+  if (track->S > 0 && track->path &&
+      cudaMemcpy((void*)d.path, track->path, sizeof(float) * 6 * track->S, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of path failed"));
+  if (track->T > 0 && track->ref &&
+      cudaMemcpy((void*)d.ref, track->ref, sizeof(float) * 13 * track->T, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of reference failed"));
+  // resident state: hover nominal, zero counts
+  std::vector<float> U;
+  fill_hover(h, U);
+  if (cudaMemcpy(d.U, U.data(), sizeof(float) * U.size(), cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of nominal failed"));
+  DevState st;
+  memset(&st, 0, sizeof st);
+  st.c_last = model->mass * model->gravity;
+  st.status = MPPI_OK;
+  if (cudaMemcpy(d.st, &st, sizeof st, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of state failed"));
+  if (cudaMemcpy(h->d_desc, &d, sizeof d, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload of descriptor failed"));
+  if (cudaMalloc(&h->d_tiles, sizeof(Tile) * h->T_cap + sizeof(int32_t) * 4) != cudaSuccess)
+    return cleanup(fail(MPPI_ERR_OOM, "tile table allocation failed"));
+  h->d_which = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(h->d_tiles) + sizeof(Tile) * h->T_cap);
+  int zero = 0;
+  if (cudaMemcpy(h->d_which, &zero, sizeof zero, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "upload failed"));
+  if ((rc = upload_tiles(h))) return cleanup(rc);
+  if ((rc = hostio_alloc(h->io, 1))) return cleanup(rc);
+  if (cudaEventCreateWithFlags(&h->ev_u0, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
+  *out = h;
+  return MPPI_OK;
+}
+
+int mppi_destroy(mppi_handle h) {
+  if (!h) return MPPI_OK;
+  {
+    // cached batch plans that reference this handle are dropped with it
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+      mppi_batch p = g_plans[i];
+      if (std::find(p->hs.begin(), p->hs.end(), h) != p->hs.end()) {
+        mppi_batch_destroy(p);
+        g_plans.erase(g_plans.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+  }
+  if (h->ev_u0) cudaEventDestroy(h->ev_u0);
+  hostio_free(h->io);
+  if (h->d_tiles) cudaFree(h->d_tiles);
+  if (h->slab) cudaFree(h->slab);
+  delete h;
+  return MPPI_OK;
+}
+
+int mppi_device_bytes(mppi_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(MPPI_ERR_ARG, "null argument");
+  *bytes = h->slab_bytes + sizeof(Tile) * h->T_cap;
+  return MPPI_OK;
+}
+
+int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
+  if (!h) return fail(MPPI_ERR_ARG, "null handle");
+  if (K < 1 || K > h->K_cap || N < 1 || N > h->N_cap)
+    return fail(MPPI_ERR_ARG, "shape K=%d N=%d outside the capacity K<=%d N<=%d", K, N, h->K_cap, h->N_cap);
+  h->params.K = K;
+  h->params.N = N;
+  h->hd.K = K;
+  h->hd.N = N;
+  h->hd.n_tiles = (K + h->block - 1) / h->block;
+  CU(cudaMemcpy(h->d_desc, &h->hd, sizeof h->hd, cudaMemcpyHostToDevice));
+  int rc = upload_tiles(h);
+  if (rc) return rc;
+  ++h->version;
+  return MPPI_OK;
+}
+
+static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
+  const SolveDesc& d = h->hd;
+  if (h->ext_noise_pending) {
+    h->ext_noise_pending = false;
+  } else {
+    CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s));
+  }
+  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, h->block, merge_cap(d.n_tiles));
+  CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s));
+  return MPPI_OK;
+}
+
+int mppi_solve(mppi_handle h, const float x0[13], double t0, void* stream, float u0_out[5]) {
+  if (!h || !x0 || !u0_out) return fail(MPPI_ERR_ARG, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LaunchIO io;
+  memset(&io, 0, sizeof io);
+  io.x0 = nullptr;
+  io.t0 = nullptr;
+  for (int i = 0; i < kNX; ++i) io.x0v[i] = x0[i];
+  io.t0v = t0;
+  io.u0 = h->io.d_u0;
+  io.status = h->io.d_status;
+  int rc = enqueue_single(h, io, s);
+  if (rc) return rc;
+  CU(cudaEventRecord(h->ev_u0, s));
+  if (h->hd.objective == MPPI_OBJ_GATE) CU(launch_nominal(h->d_desc, h->d_which, 1, s));
+  CU(cudaEventSynchronize(h->ev_u0));
+  for (int i = 0; i < kNU; ++i) u0_out[i] = ((volatile float*)h->io.u0)[i];
+  const int st = ((volatile int32_t*)h->io.status)[0];
+  if (st == MPPI_WARN_DEGENERATE) return fail(MPPI_WARN_DEGENERATE, "every sample cost was non-finite");
+  return MPPI_OK;
+}
+
+int mppi_solve_async(mppi_handle h, const float* d_x0, double t0, void* stream, float* d_u0) {
+  if (!h || !d_x0 || !d_u0) return fail(MPPI_ERR_ARG, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LaunchIO io;
+  memset(&io, 0, sizeof io);
+  io.x0 = d_x0;
+  io.t0 = nullptr;
+  io.t0v = t0;
+  io.u0 = d_u0;
+  io.status = nullptr;
+  int rc = enqueue_single(h, io, s);
+  if (rc) return rc;
+  if (h->hd.objective == MPPI_OBJ_GATE) CU(launch_nominal(h->d_desc, h->d_which, 1, s));
+  return MPPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state access
+// ---------------------------------------------------------------------------
+int mppi_get_nominal(mppi_handle h, float* U) {
+  if (!h || !U) return fail(MPPI_ERR_ARG, "null argument");
+  CU(cudaMemcpy(U, h->hd.U, sizeof(float) * h->hd.N * kNU, cudaMemcpyDeviceToHost));
+  return MPPI_OK;
+}
+int mppi_get_unew(mppi_handle h, float* U) {
+  if (!h || !U) return fail(MPPI_ERR_ARG, "null argument");
+  CU(cudaMemcpy(U, h->hd.unew, sizeof(float) * h->hd.N * kNU, cudaMemcpyDeviceToHost));
+  return MPPI_OK;
+}
+int mppi_get_costs(mppi_handle h, double* J) {
+  if (!h || !J) return fail(MPPI_ERR_ARG, "null argument");
+  CU(cudaMemcpy(J, h->hd.J, sizeof(double) * h->hd.K, cudaMemcpyDeviceToHost));
+  return MPPI_OK;
+}
+int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass) {
+  if (!h) return fail(MPPI_ERR_ARG, "null handle");
+  std::vector<int32_t> info(h->hd.K);
+  CU(cudaMemcpy(info.data(), h->hd.info, sizeof(int32_t) * h->hd.K, cudaMemcpyDeviceToHost));
+  for (int m = 0; m < h->hd.K; ++m) {
+    if (npass) npass[m] = info[m] & 0xFFFF;
+    if (first_pass) first_pass[m] = (info[m] >> 16) - 1;
+  }
+  return MPPI_OK;
+}
+int mppi_get_noise(mppi_handle h, float* Z) {
+  if (!h || !Z) return fail(MPPI_ERR_ARG, "null argument");
+  const SolveDesc& d = h->hd;
+  const size_t nk = (size_t)d.N * d.K;
+  std::vector<float> z4(nk * 4), z5(h->nu == 5 ? nk : 0);
+  if (d.noise_bf16) {
+    std::vector<uint16_t> b(nk * 4), b5(h->nu == 5 ? nk : 0);
+    CU(cudaMemcpy(b.data(), d.Zb, nk * 8, cudaMemcpyDeviceToHost));
+    if (h->nu == 5) CU(cudaMemcpy(b5.data(), d.Z5b, nk * 2, cudaMemcpyDeviceToHost));
+    auto widen = [](uint16_t v) {
+      uint32_t w = (uint32_t)v << 16;
+      float f;
+      memcpy(&f, &w, 4);
+      return f;
+    };
+    for (size_t i = 0; i < nk * 4; ++i) z4[i] = widen(b[i]);
+    for (size_t i = 0; i < z5.size(); ++i) z5[i] = widen(b5[i]);
+  } else {
+    CU(cudaMemcpy(z4.data(), d.Z4, nk * 16, cudaMemcpyDeviceToHost));
+    if (h->nu == 5) CU(cudaMemcpy(z5.data(), d.Z5, nk * 4, cudaMemcpyDeviceToHost));
+  }
+  for (size_t i = 0; i < nk; ++i) {
+    for (int j = 0; j < 4; ++j) Z[i * 5 + j] = z4[i * 4 + j];
+    Z[i * 5 + 4] = h->nu == 5 ? z5[i] : 0.f;
+  }
+  return MPPI_OK;
+}
+int mppi_get_passcnt(mppi_handle h, int32_t* passcnt) {
+  if (!h || !passcnt) return fail(MPPI_ERR_ARG, "null argument");
+  CU(cudaMemcpy(passcnt, h->hd.passcnt, sizeof(int32_t) * (h->hd.N + 1), cudaMemcpyDeviceToHost));
+  return MPPI_OK;
+}
+int mppi_get_info(mppi_handle h, int32_t info[4]) {
+  if (!h || !info) return fail(MPPI_ERR_ARG, "null argument");
+  DevState st;
+  CU(cudaMemcpy(&st, h->hd.st, sizeof st, cudaMemcpyDeviceToHost));
+  info[0] = st.gate0;
+  info[1] = st.status;
+  info[2] = (int32_t)st.iter;
+  info[3] = st.gate;
+  return MPPI_OK;
+}
+int mppi_get_solve_scalars(mppi_handle h, double out[4]) {
+  if (!h || !out) return fail(MPPI_ERR_ARG, "null argument");
+  DevState st;
+  CU(cudaMemcpy(&st, h->hd.st, sizeof st, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) out[i] = st.scal[i];
+  return MPPI_OK;
+}
+int mppi_get_xref(mppi_handle h, float* xref) {
+  if (!h || !xref) return fail(MPPI_ERR_ARG, "null argument");
+  CU(cudaMemcpy(xref, h->hd.xref, sizeof(float) * 13 * (h->hd.N + 1), cudaMemcpyDeviceToHost));
+  return MPPI_OK;
+}
+
+// serialised state: header, DevState, U [N_cap][5], prevcnt [N_cap]
+struct StateHeader {
+  uint32_t magic, version, N_cap, nu;
+};
+static const uint32_t kMagic = 0x4D505049u;  // "MPPI"
+
+int mppi_export_state(mppi_handle h, void* buf, size_t* size) {
+  if (!h || !size) return fail(MPPI_ERR_ARG, "null argument");
+  const size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(float) * h->N_cap * kNU +
+                      sizeof(int32_t) * h->N_cap;
+  if (!buf) {
+    *size = need;
+    return MPPI_OK;
+  }
+  if (*size < need) return fail(MPPI_ERR_ARG, "buffer of %zu bytes, need %zu", *size, need);
+  char* c = static_cast<char*>(buf);
+  StateHeader hd{kMagic, 1u, (uint32_t)h->N_cap, (uint32_t)h->nu};
+  memcpy(c, &hd, sizeof hd);
+  c += sizeof hd;
+  CU(cudaMemcpy(c, h->hd.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  c += sizeof(DevState);
+  CU(cudaMemcpy(c, h->hd.U, sizeof(float) * h->N_cap * kNU, cudaMemcpyDeviceToHost));
+  c += sizeof(float) * h->N_cap * kNU;
+  CU(cudaMemcpy(c, h->hd.prevcnt, sizeof(int32_t) * h->N_cap, cudaMemcpyDeviceToHost));
+  *size = need;
+  return MPPI_OK;
+}
+
+int mppi_import_state(mppi_handle h, const void* buf, size_t size) {
+  if (!h || !buf) return fail(MPPI_ERR_ARG, "null argument");
+  const size_t need = sizeof(StateHeader) + sizeof(DevState) + sizeof(float) * h->N_cap * kNU +
+                      sizeof(int32_t) * h->N_cap;
+  if (size < need) return fail(MPPI_ERR_ARG, "state blob of %zu bytes, need %zu", size, need);
+  const char* c = static_cast<const char*>(buf);
+  StateHeader hd;
+  memcpy(&hd, c, sizeof hd);
+  if (hd.magic != kMagic || hd.version != 1u || (int)hd.N_cap != h->N_cap || (int)hd.nu != h->nu)
+    return fail(MPPI_ERR_ARG, "state blob does not match this handle");
+  c += sizeof hd;
+  CU(cudaMemcpy(h->hd.st, c, sizeof(DevState), cudaMemcpyHostToDevice));
+  c += sizeof(DevState);
+  CU(cudaMemcpy(h->hd.U, c, sizeof(float) * h->N_cap * kNU, cudaMemcpyHostToDevice));
+  c += sizeof(float) * h->N_cap * kNU;
+  CU(cudaMemcpy(h->hd.prevcnt, c, sizeof(int32_t) * h->N_cap, cudaMemcpyHostToDevice));
+  return MPPI_OK;
+}
+
+int mppi_set_gate_index(mppi_handle h, int32_t gate) {
+  if (!h) return fail(MPPI_ERR_ARG, "null handle");
+  CU(cudaMemcpy(&h->hd.st->gate, &gate, sizeof gate, cudaMemcpyHostToDevice));
+  return MPPI_OK;
+}
+
+int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* stream) {
+  if (!h || !d_Z) return fail(MPPI_ERR_ARG, "null argument");
+  if (h->nu == 5 && !d_Z5) return fail(MPPI_ERR_ARG, "contouring needs the 5th noise column");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const SolveDesc& d = h->hd;
+  const size_t nk = (size_t)d.N * d.K;
+  const size_t el = d.noise_bf16 ? 2 : 4;
+  CU(cudaMemcpyAsync(d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4, d_Z, nk * 4 * el, cudaMemcpyDeviceToDevice, s));
+  if (h->nu == 5)
+    CU(cudaMemcpyAsync(d.noise_bf16 ? (void*)d.Z5b : (void*)d.Z5, d_Z5, nk * el, cudaMemcpyDeviceToDevice, s));
+  h->ext_noise_pending = true;
+  return MPPI_OK;
+}
+
+int mppi_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int32_t n,
+                uint32_t* d_out, void* stream) {
+  if (n < 0 || (n > 0 && !d_out)) return fail(MPPI_ERR_ARG, "bad arguments");
+  CU(launch_philox(k0, k1, c0, c1, c2, c3, n, d_out, static_cast<cudaStream_t>(stream)));
+  return MPPI_OK;
+}
+
+int mppi_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int32_t n, float* d_out,
+                 void* stream) {
+  if (n < 0 || (n > 0 && !d_out)) return fail(MPPI_ERR_ARG, "bad arguments");
+  CU(launch_normals(seed, drone, k, it, blk, n, d_out, static_cast<cudaStream_t>(stream)));
+  return MPPI_OK;
+}
+
+int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
+                        const float* d_U, float* d_X, void* stream) {
+  if (!model || N < 1 || B < 0 || (B > 0 && (!d_x0 || !d_U || !d_X))) return fail(MPPI_ERR_ARG, "bad arguments");
+  SolveDesc md;
+  memset(&md, 0, sizeof md);
+  md.inv_mass = (float)(1.0 / (double)model->mass);
+  md.gravity = model->gravity;
+  md.k_omega = model->k_omega;
+  const double Jx = model->inertia[0], Jy = model->inertia[1], Jz = model->inertia[2];
+  md.gyro[0] = (float)((Jz - Jy) / Jx);
+  md.gyro[1] = (float)((Jx - Jz) / Jy);
+  md.gyro[2] = (float)((Jy - Jx) / Jz);
+  for (int i = 0; i < 3; ++i) md.drag[i] = model->drag[i];
+  md.has_drag = (model->drag[0] != 0.f || model->drag[1] != 0.f || model->drag[2] != 0.f) ? 1 : 0;
+  CU(launch_rollout_states(md, dt, N, B, d_x0, d_U, d_X, static_cast<cudaStream_t>(stream)));
+  return MPPI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
+  for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s));
+  for (const auto& g : b->rollout_groups)
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s));
+  return MPPI_OK;
+}
+
+int mppi_batch_destroy(mppi_batch b) {
+  if (!b) return MPPI_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->ev) cudaEventDestroy(b->ev);
+  hostio_free(b->io);
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+  return MPPI_OK;
+}
+
+int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_batch* out) {
+  if (!out || n < 1 || !hs) return fail(MPPI_ERR_ARG, "bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return fail(MPPI_ERR_ARG, "null handle at %d", i);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (hs[i] == hs[j]) return fail(MPPI_ERR_ARG, "handle %d appears twice in the batch", i);
+  mppi_batch b = new mppi_batch_s();
+  b->n = n;
+  b->hs.assign(hs, hs + n);
+  for (int i = 0; i < n; ++i) b->versions.push_back(hs[i]->version);
+  b->use_graph = use_graph != 0;
+  // group tiles by launch configuration; longest horizons first (LPT)
+  struct Key {
+    int obj, bf16, block;
+    bool operator<(const Key& o) const {
+      return obj != o.obj ? obj < o.obj : bf16 != o.bf16 ? bf16 < o.bf16 : block < o.block;
+    }
+  };
+  std::vector<std::pair<Key, std::vector<Tile>>> rg;
+  std::vector<std::pair<Key, std::vector<Tile>>> ng;
+  std::vector<uint32_t> rsmem;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return (long long)hs[a]->hd.N * hs[a]->hd.K > (long long)hs[c]->hd.N * hs[c]->hd.K;
+  });
+  std::vector<int32_t> which;
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = order[oi];
+    const SolveDesc& d = hs[i]->hd;
+    Key k{d.objective, d.noise_bf16, d.block};
+    Key kn{0, d.noise_bf16, d.block};
+    auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
+      for (size_t j = 0; j < v.size(); ++j)
+        if (!(v[j].first < key) && !(key < v[j].first)) return (int)j;
+      v.push_back({key, {}});
+      return (int)v.size() - 1;
+    };
+    int gi = find(rg, k);
+    if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
+    rsmem[gi] = std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, d.block, merge_cap(d.n_tiles)));
+    int gn = find(ng, kn);
+    for (int t = 0; t < d.n_tiles; ++t) {
+      rg[gi].second.push_back(Tile{i, t * d.block});
+      ng[gn].second.push_back(Tile{i, t * d.block});
+    }
+    if (d.objective == MPPI_OBJ_GATE) which.push_back(i);
+  }
+  size_t tiles_total = 0;
+  for (auto& g : rg) tiles_total += g.second.size();
+  for (auto& g : ng) tiles_total += g.second.size();
+  const size_t bytes = al256(sizeof(SolveDesc) * n) + al256(sizeof(Tile) * tiles_total) + al256(sizeof(int32_t) * (which.size() + 1));
+  if (cudaMalloc(&b->dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(MPPI_ERR_OOM, "batch allocation failed");
+  }
+  char* c = static_cast<char*>(b->dev);
+  b->d_descs = reinterpret_cast<SolveDesc*>(c);
+  std::vector<SolveDesc> descs(n);
+  for (int i = 0; i < n; ++i) descs[i] = hs[i]->hd;
+  auto cleanup = [&](int code) {
+    mppi_batch_destroy(b);
+    return code;
+  };
+  if (cudaMemcpy(b->d_descs, descs.data(), sizeof(SolveDesc) * n, cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "descriptor upload failed"));
+  c += al256(sizeof(SolveDesc) * n);
+  Tile* tp = reinterpret_cast<Tile*>(c);
+  for (size_t gi = 0; gi < rg.size(); ++gi) {
+    auto& v = rg[gi].second;
+    if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
+      return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
+    b->rollout_groups.push_back({rg[gi].first.obj, rg[gi].first.bf16, rg[gi].first.block, rsmem[gi], (int)v.size(), tp});
+    tp += v.size();
+  }
+  for (auto& g : ng) {
+    auto& v = g.second;
+    if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
+      return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
+    b->noise_groups.push_back({g.first.bf16, g.first.block, (int)v.size(), tp});
+    tp += v.size();
+  }
+  c += al256(sizeof(Tile) * tiles_total);
+  b->d_which = reinterpret_cast<int32_t*>(c);
+  b->n_which = (int)which.size();
+  if (!which.empty() && cudaMemcpy(b->d_which, which.data(), sizeof(int32_t) * which.size(), cudaMemcpyHostToDevice))
+    return cleanup(fail(MPPI_ERR_CUDA, "work list upload failed"));
+  int rc = hostio_alloc(b->io, n);
+  if (rc) return cleanup(rc);
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
+  if (b->use_graph) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(MPPI_ERR_CUDA, "stream creation failed"));
+    LaunchIO io;
+    memset(&io, 0, sizeof io);
+    io.x0 = b->io.d_x0;
+    io.t0 = b->io.d_t0;
+    io.u0 = b->io.d_u0;
+    io.status = b->io.d_status;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
+    int rc2 = batch_enqueue(b, io, b->cap_stream);
+    cudaError_t e1 = cudaEventRecord(b->ev, b->cap_stream);
+    cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
+    cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (rc2 || e1 || e2 || e3) return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed"));
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+      return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
+  }
+  *out = b;
+  return MPPI_OK;
+}
+
+static int batch_check(mppi_batch b) {
+  for (int i = 0; i < b->n; ++i)
+    if (b->hs[i]->version != b->versions[i]) return fail(MPPI_ERR_ARG, "handle %d changed shape since the batch was planned", i);
+  for (int i = 0; i < b->n; ++i)
+    if (b->hs[i]->ext_noise_pending) return fail(MPPI_ERR_ARG, "caller noise is only supported for single solves");
+  return MPPI_OK;
+}
+
+int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* stream, float* u0s_out) {
+  if (!b || !x0s || !u0s_out) return fail(MPPI_ERR_ARG, "null argument");
+  int rc = batch_check(b);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  memcpy(b->io.x0, x0s, sizeof(float) * 13 * b->n);
+  if (t0s)
+    memcpy(b->io.t0, t0s, sizeof(double) * b->n);
+  else
+    memset(b->io.t0, 0, sizeof(double) * b->n);
+  if (b->use_graph) {
+    CU(cudaGraphLaunch(b->exec, s));
+  } else {
+    LaunchIO io;
+    memset(&io, 0, sizeof io);
+    io.x0 = b->io.d_x0;
+    io.t0 = b->io.d_t0;
+    io.u0 = b->io.d_u0;
+    io.status = b->io.d_status;
+    rc = batch_enqueue(b, io, s);
+    if (rc) return rc;
+    CU(cudaEventRecord(b->ev, s));
+    CU(launch_nominal(b->d_descs, b->d_which, b->n_which, s));
+  }
+  CU(cudaEventSynchronize(b->ev));
+  memcpy(u0s_out, (const void*)b->io.u0, sizeof(float) * 5 * b->n);
+  for (int i = 0; i < b->n; ++i)
+    if (((volatile int32_t*)b->io.status)[i] == MPPI_WARN_DEGENERATE)
+      return fail(MPPI_WARN_DEGENERATE, "solve %d: every sample cost was non-finite", i);
+  return MPPI_OK;
+}
+
+int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s, void* stream, float* d_u0s) {
+  if (!b || !d_x0s || !d_u0s) return fail(MPPI_ERR_ARG, "null argument");
+  int rc = batch_check(b);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LaunchIO io;
+  memset(&io, 0, sizeof io);
+  io.x0 = d_x0s;
+  io.t0 = d_t0s;
+  io.u0 = d_u0s;
+  io.status = nullptr;
+  if (!d_t0s) return fail(MPPI_ERR_ARG, "d_t0s is required");
+  rc = batch_enqueue(b, io, s);
+  if (rc) return rc;
+  CU(launch_nominal(b->d_descs, b->d_which, b->n_which, s));
+  return MPPI_OK;
+}
+
+// mppi_solve_batch: cached plans keyed by the handle list (g_plans)
+
+int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const double* t0s, void* stream,
+                     float* u0s_out) {
+  if (n < 1 || !hs || !x0s || !u0s_out) return fail(MPPI_ERR_ARG, "bad arguments");
+  mppi_batch plan = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (size_t i = 0; i < g_plans.size(); ++i) {
+      mppi_batch p = g_plans[i];
+      if (p->n != n || !std::equal(p->hs.begin(), p->hs.end(), hs)) continue;
+      bool fresh = true;
+      for (int j = 0; j < n; ++j) fresh = fresh && p->versions[j] == hs[j]->version;
+      if (fresh) {
+        plan = p;
+      } else {
+        mppi_batch_destroy(p);
+        g_plans.erase(g_plans.begin() + i);
+      }
+      break;
+    }
+    if (!plan) {
+      int rc = mppi_batch_create(n, hs, 1, &plan);
+      if (rc) return rc;
+      if (g_plans.size() >= 8) {
+        mppi_batch_destroy(g_plans.front());
+        g_plans.erase(g_plans.begin());
+      }
+      g_plans.push_back(plan);
+    }
+  }
+  return mppi_batch_solve(plan, x0s, t0s, stream, u0s_out);
+}
+
+}  // extern "C"

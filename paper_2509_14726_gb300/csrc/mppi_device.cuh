@@ -1,0 +1,311 @@
+// mppi_device.cuh -- device-side data layout and per-thread arithmetic of one
+// MPPI solve (arXiv 2509.14726, Sec. III-IV) for sm_103a.
+//
+// One thread owns one sample: its 13-D state lives in registers for the whole
+// horizon, positions and velocities carry a compensation term (Kahan), and the
+// cost is accumulated in a float hi/lo pair.  Everything a block shares (the
+// nominal U*, gates, path table, reference window) sits in shared memory.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/mppi.h"
+
+namespace mppi {
+
+constexpr int kNX = 13;
+constexpr int kNU = 5;
+constexpr int kMaxN = MPPI_MAX_N;
+constexpr int kMaxGates = MPPI_MAX_GATES;
+constexpr int kMaxBlock = 512;
+
+// --------------------------------------------------------------------------
+// resident per-drone controller state (device memory, one per handle)
+// --------------------------------------------------------------------------
+struct DevState {
+  int32_t gate;        // absolute index of the targeted gate
+  uint32_t iter;       // Philox iteration (counter word 2)
+  int32_t has_prev;    // prev_x0 valid
+  int32_t has_theta;   // theta / v_theta valid (contouring)
+  int32_t n_nom;       // rows of U that came from a solve (0: hover init)
+  int32_t n_prev;      // entries of prevcnt that came from a solve
+  int32_t gate0;       // gate index at the start of the last solve
+  int32_t adv;         // gates the plant passed between the last two solves
+  int32_t status;      // mppi_status of the last solve
+  int32_t timeouts;    // bounded waits that gave up (diagnostics)
+  double theta;        // progress at the start of the last solve
+  double v_theta;      // progress speed for the next solve
+  float c_last;        // last applied collective thrust
+  float prev_x0[kNX];  // x0 of the last solve
+  double scal[4];      // theta0, v_theta0, J_min, sum of exp weights
+};
+
+// --------------------------------------------------------------------------
+// per-handle solve descriptor (device memory, read by every block)
+// --------------------------------------------------------------------------
+struct SolveDesc {
+  // model (Eq. 2, CTBR input)
+  float mass, inv_mass, gravity, k_omega;
+  float gyro[3];        // (Jz-Jy)/Jx, (Jx-Jz)/Jy, (Jy-Jx)/Jz
+  float drag[3];
+  int32_t has_drag;
+  float u_min[kNU], u_max[kNU];
+  float omega_max, z_floor;
+  // sampling and weights (Eq. 3, Eq. 4)
+  int32_t objective, K, N, nu;
+  float dt, lambda, inv_lambda;
+  float sigma[kNU];
+  uint32_t seed, drone_id;
+  int32_t noise_bf16, accum;
+  // costs
+  float w_limit, q_near, r_near2;
+  int32_t temporal_rule;
+  float q_lag, q_cont, q_omega[3], r_dv, r_dthrust, mu, v_theta_max, theta_back, theta_ahead;
+  float Q[kNX], QN[kNX], R[4];
+  float hover;
+  // track (device pointers)
+  const float* gates;   // [n][6]
+  int32_t n_gates, closed;
+  const float* path;    // [S][6]
+  int32_t S;
+  float L, ds, inv_ds;
+  const float* ref;     // [T][13]
+  int32_t T;
+  float dt_ref;
+  // resident state
+  DevState* st;
+  float* U;             // [N_cap][5] (+pad), always fully populated
+  int32_t* prevcnt;     // [N_cap] (+pad), always fully populated
+  int32_t N_cap;
+  // per-solve buffers
+  float4* Z4;           // [N][K] standard normals (F32 storage)
+  uint2* Zb;            // [N][K] 4 x bf16 (BF16 storage)
+  float* Z5;            // [N][K] 5th normal (contouring, F32)
+  __nv_bfloat16* Z5b;   // [N][K] 5th normal (contouring, BF16)
+  double* J;            // [K]
+  int32_t* info;        // [K] npass | (first_pass + 1) << 16
+  double* part_m;       // [tiles] per-tile minimum cost
+  double* part_S;       // [tiles] per-tile sum of exp weights
+  double* part_P;       // [tiles][N][5] per-tile weighted deviation sums
+  uint32_t* ticket;     // blocks of this solve that finished
+  float* unew;          // [N][5] Eq. 5 result before the shift
+  int32_t* passcnt;     // [N+1] gates passed along the new nominal
+  float* xref;          // [N+1][13] tracking window used (diagnostics)
+  int32_t n_tiles, block;
+  int32_t ext_noise;    // 1: use the caller's noise for this solve
+};
+
+// device-side per-launch inputs and outputs (indexed by the solve's position
+// in the batch); pointers may be device or mapped host memory
+struct LaunchIO {
+  const float* x0;      // [n][13]; nullptr: use x0v (single solve)
+  const double* t0;     // [n];     nullptr: use t0v
+  float* u0;            // [n][5]
+  int32_t* status;      // [n] mppi_status of each solve (may be nullptr)
+  float x0v[kNX];
+  double t0v;
+};
+
+// tile -> (solve position, first sample)
+struct Tile {
+  int32_t solve;
+  int32_t m0;
+};
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// uniform in (0, 1] from the top 24 bits; exact in binary32
+__device__ __forceinline__ float u24(uint32_t x) { return (float)((x >> 8) + 1u) * 5.9604644775390625e-8f; }
+
+__device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb) {
+  const float r = sqrtf(-2.0f * logf(u24(xa)));
+  float s, c;
+  sincospif(2.0f * u24(xb), &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+__device__ __forceinline__ float4 normals4(uint32_t seed, uint32_t drone, uint32_t m, uint32_t k,
+                                           uint32_t iter, uint32_t blk) {
+  const uint4 x = philox4x32_10(make_uint4(m, k, iter, blk), seed, drone);
+  const float2 a = box_muller(x.x, x.y), b = box_muller(x.z, x.w);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// --------------------------------------------------------------------------
+// small helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// Kahan step: s + y with the running compensation c (true sum ~ s - c)
+__device__ __forceinline__ void kahan_add(float& s, float& c, float y) {
+  const float yy = y - c;
+  const float t = s + yy;
+  c = (t - s) - yy;
+  s = t;
+}
+
+// error-free sum (Knuth TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// --------------------------------------------------------------------------
+// quadrotor state and the RK4 step (Eq. 2 with CTBR; classical RK4, ZOH input)
+// --------------------------------------------------------------------------
+struct Quad {
+  float px, py, pz, cpx, cpy, cpz;  // position + Kahan compensation
+  float vx, vy, vz, cvx, cvy, cvz;  // velocity + Kahan compensation
+  float qw, qx, qy, qz;
+  float wx, wy, wz;
+};
+
+struct ModelRegs {
+  float inv_mass, gravity, k_omega, g0, g1, g2, d0, d1, d2;
+  int has_drag;
+};
+
+__device__ __forceinline__ void accel(const ModelRegs& M, float ac, float qw, float qx, float qy, float qz,
+                                      float vx, float vy, float vz, float& ax, float& ay, float& az) {
+  // thrust along the body z axis: R(q) e_z
+  const float bx = 2.0f * (qx * qz + qw * qy);
+  const float by = 2.0f * (qy * qz - qw * qx);
+  const float bz = 1.0f - 2.0f * (qx * qx + qy * qy);
+  ax = ac * bx;
+  ay = ac * by;
+  az = ac * bz - M.gravity;
+  if (M.has_drag) {
+    // - R D R^T v
+    const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = bx;
+    const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = by;
+    const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = bz;
+    const float bv0 = M.d0 * (r00 * vx + r10 * vy + r20 * vz);
+    const float bv1 = M.d1 * (r01 * vx + r11 * vy + r21 * vz);
+    const float bv2 = M.d2 * (r02 * vx + r12 * vy + r22 * vz);
+    ax -= r00 * bv0 + r01 * bv1 + r02 * bv2;
+    ay -= r10 * bv0 + r11 * bv1 + r12 * bv2;
+    az -= r20 * bv0 + r21 * bv1 + r22 * bv2;
+  }
+}
+
+__device__ __forceinline__ void attitude_rate(const ModelRegs& M, float kcx, float kcy, float kcz, float qw,
+                                              float qx, float qy, float qz, float wx, float wy, float wz,
+                                              float& dqw, float& dqx, float& dqy, float& dqz, float& dwx,
+                                              float& dwy, float& dwz) {
+  const float hx = 0.5f * wx, hy = 0.5f * wy, hz = 0.5f * wz;
+  dqw = -(qx * hx + qy * hy + qz * hz);
+  dqx = qw * hx + qy * hz - qz * hy;
+  dqy = qw * hy + qz * hx - qx * hz;
+  dqz = qw * hz + qx * hy - qy * hx;
+  // tau = J k_w (w_cmd - w):  w_dot = k_w (w_cmd - w) - J^-1 (w x J w)
+  dwx = kcx - M.k_omega * wx - M.g0 * wy * wz;
+  dwy = kcy - M.k_omega * wy - M.g1 * wz * wx;
+  dwz = kcz - M.k_omega * wz - M.g2 * wx * wy;
+}
+
+// One RK4 step with the input (c, w_cmd) held.  Writes the position increment
+// (the exact RK4 increment, before compensated accumulation) to dp.
+__device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, float cx, float cy, float cz,
+                                         float h, float& dpx, float& dpy, float& dpz) {
+  const float ac = c * M.inv_mass;
+  const float kcx = M.k_omega * cx, kcy = M.k_omega * cy, kcz = M.k_omega * cz;
+  const float h2 = 0.5f * h;
+  float dqw, dqx, dqy, dqz, dwx, dwy, dwz, ax, ay, az;
+  // stage 1
+  attitude_rate(M, kcx, kcy, kcz, s.qw, s.qx, s.qy, s.qz, s.wx, s.wy, s.wz, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  accel(M, ac, s.qw, s.qx, s.qy, s.qz, s.vx, s.vy, s.vz, ax, ay, az);
+  float sqw = dqw, sqx = dqx, sqy = dqy, sqz = dqz, swx = dwx, swy = dwy, swz = dwz;
+  float sax = ax, say = ay, saz = az;  // acc1 + 2 acc2 + 2 acc3 + acc4
+  float pax = ax, pay = ay, paz = az;  // acc1 + acc2 + acc3 (position increment)
+  // stage 2
+  float qw2 = s.qw + h2 * dqw, qx2 = s.qx + h2 * dqx, qy2 = s.qy + h2 * dqy, qz2 = s.qz + h2 * dqz;
+  float wx2 = s.wx + h2 * dwx, wy2 = s.wy + h2 * dwy, wz2 = s.wz + h2 * dwz;
+  float vx2 = s.vx + h2 * ax, vy2 = s.vy + h2 * ay, vz2 = s.vz + h2 * az;
+  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
+  swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
+  sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
+  pax += ax; pay += ay; paz += az;
+  // stage 3
+  qw2 = s.qw + h2 * dqw; qx2 = s.qx + h2 * dqx; qy2 = s.qy + h2 * dqy; qz2 = s.qz + h2 * dqz;
+  wx2 = s.wx + h2 * dwx; wy2 = s.wy + h2 * dwy; wz2 = s.wz + h2 * dwz;
+  vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az;
+  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
+  swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
+  sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
+  pax += ax; pay += ay; paz += az;
+  // stage 4
+  qw2 = s.qw + h * dqw; qx2 = s.qx + h * dqx; qy2 = s.qy + h * dqy; qz2 = s.qz + h * dqz;
+  wx2 = s.wx + h * dwx; wy2 = s.wy + h * dwy; wz2 = s.wz + h * dwz;
+  vx2 = s.vx + h * ax; vy2 = s.vy + h * ay; vz2 = s.vz + h * az;
+  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  sqw += dqw; sqx += dqx; sqy += dqy; sqz += dqz;
+  swx += dwx; swy += dwy; swz += dwz;
+  sax += ax; say += ay; saz += az;
+  // combine: p += h v + h^2/6 (a1 + a2 + a3), v += h/6 (a1 + 2 a2 + 2 a3 + a4)
+  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+  dpx = h * s.vx + hh6 * pax;
+  dpy = h * s.vy + hh6 * pay;
+  dpz = h * s.vz + hh6 * paz;
+  kahan_add(s.px, s.cpx, dpx);
+  kahan_add(s.py, s.cpy, dpy);
+  kahan_add(s.pz, s.cpz, dpz);
+  kahan_add(s.vx, s.cvx, h6 * sax);
+  kahan_add(s.vy, s.cvy, h6 * say);
+  kahan_add(s.vz, s.cvz, h6 * saz);
+  float qw1 = s.qw + h6 * sqw, qx1 = s.qx + h6 * sqx, qy1 = s.qy + h6 * sqy, qz1 = s.qz + h6 * sqz;
+  s.wx += h6 * swx;
+  s.wy += h6 * swy;
+  s.wz += h6 * swz;
+  const float rn = rsqrtf(qw1 * qw1 + qx1 * qx1 + qy1 * qy1 + qz1 * qz1);
+  s.qw = qw1 * rn;
+  s.qx = qx1 * rn;
+  s.qy = qy1 * rn;
+  s.qz = qz1 * rn;
+}
+
+// compensated position (hi - compensation)
+__device__ __forceinline__ float pxt(const Quad& s) { return s.px - s.cpx; }
+__device__ __forceinline__ float pyt(const Quad& s) { return s.py - s.cpy; }
+__device__ __forceinline__ float pzt(const Quad& s) { return s.pz - s.cpz; }
+
+__device__ __forceinline__ float limit_penalty(float wlim, float wmax, float zf, const Quad& s) {
+  const float ex = fmaxf(fabsf(s.wx) - wmax, 0.f), ey = fmaxf(fabsf(s.wy) - wmax, 0.f),
+              ez = fmaxf(fabsf(s.wz) - wmax, 0.f);
+  const float e = fmaxf(zf - pzt(s), 0.f);
+  return wlim * (ex * ex + ey * ey + ez * ez + e * e);
+}
+
+// gate frame in shared memory: centre, plane normal (horizontal), half sizes
+struct GateF {
+  float cx, cy, cz, nx, ny, hw, hh, pad;
+};
+
+}  // namespace mppi

@@ -1,0 +1,977 @@
+// mppi_kernels.cu -- the sm_103a kernels of one MPPI solve (arXiv 2509.14726).
+//
+//   noise_kernel     Eq. 3: Philox4x32-10 -> Box-Muller standard normals,
+//                    stored [N][K] so that a warp writes 512 contiguous bytes.
+//   rollout_kernel   Eq. 2 + Eq. 6-9: one thread per sample, RK4 in registers,
+//                    objective and feasibility penalty per step; then Eq. 4/5
+//                    in flash-softmax form: each block reduces its samples to
+//                    (local min cost, sum of exp weights, weighted deviation
+//                    sums per (step, input)) and the last block of a group /
+//                    of the solve merges those partials, writes U*_new and
+//                    u0, shifts the nominal (warm start) and advances the
+//                    controller state.  No grid-wide wait: an atomic ticket
+//                    picks the merging block.
+//   nominal_kernel   rollout of U*_new from x0 with the gate logic: the gate
+//                    pass counts that the temporal-consistency rule of the next
+//                    solve reads (Sec. IV-A).
+#include <cfloat>
+#include <cmath>
+
+#include "mppi_device.cuh"
+#include "mppi_launch.h"
+
+namespace mppi {
+
+// bounded wait on an mbarrier phase; returns false after ~timeout_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > timeout_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+// TMA bulk copy global -> shared (16-byte aligned, size multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide reductions through a small shared scratch (>= 32 doubles)
+__device__ double block_min_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_min_d(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = INFINITY;
+  for (int i = 0; i < nw; ++i) r = fmin(r, red[i]);
+  return r;
+}
+__device__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < nw; ++i) r += red[i];  // fixed order: deterministic
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// gate geometry (Sec. IV-A): s = n . (p - c); a pass goes from s < 0 to s >= 0
+// through the opening (lateral |l . e| <= half_w, vertical |e_z| <= half_h)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float plane_dist(const GateF& g, float x, float y) {
+  return g.nx * (x - g.cx) + g.ny * (y - g.cy);
+}
+
+__device__ __forceinline__ bool through_opening(const GateF& g, float sa, float sb, float ax, float ay, float az,
+                                                float dx, float dy, float dz) {
+  const float a = sa / (sa - sb);
+  const float ex = ax + a * dx - g.cx, ey = ay + a * dy - g.cy, ez = az + a * dz - g.cz;
+  const float lat = -g.ny * ex + g.nx * ey;
+  return fabsf(lat) <= g.hw && fabsf(ez) <= g.hh;
+}
+
+__device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
+  if (closed) {
+    int r = idx % n;
+    return r < 0 ? r + n : r;
+  }
+  return idx < n ? idx : n - 1;
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of the rollout kernel
+// ---------------------------------------------------------------------------
+struct SmemLayout {
+  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_merge, total;
+};
+
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, int block, int merge_cap,
+                                                  int path_in_smem) {
+  SmemLayout L;
+  uint32_t o = 0;
+  L.off_U = o;
+  o += align16((uint32_t)N * kNU * 4u);
+  L.off_prev = o;
+  o += align16((uint32_t)N * 4u);
+  L.off_gates = o;
+  o += align16((uint32_t)kMaxGates * sizeof(GateF));
+  L.off_path = o;
+  if (objective == MPPI_OBJ_CONTOUR && path_in_smem) o += align16((uint32_t)S * 6u * 4u);
+  L.off_xref = o;
+  if (objective == MPPI_OBJ_TRACK) o += align16((uint32_t)(N + 1) * kNX * 4u);
+  L.off_e = o;
+  o += align16((uint32_t)block * 4u);
+  L.off_merge = o;
+  o += align16((uint32_t)merge_cap * 8u);
+  L.total = o;
+  return L;
+}
+
+__host__ __device__ int path_fits_smem(int S) { return S > 0 && S * 24 <= 96 * 1024; }
+
+uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap) {
+  return smem_layout(N, objective, S, block, merge_cap, path_fits_smem(S)).total;
+}
+
+// ---------------------------------------------------------------------------
+// K1: noise
+// ---------------------------------------------------------------------------
+template <int BF16>
+__global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __restrict__ descs,
+                                                          const Tile* __restrict__ tiles) {
+  const Tile tile = tiles[blockIdx.x];
+  const SolveDesc& d = descs[tile.solve];
+  const int K = d.K, N = d.N;
+  const int m = tile.m0 + threadIdx.x;
+  if (d.ext_noise || m >= K || threadIdx.x >= d.block) return;
+  const uint32_t iter = d.st->iter;
+  const bool five = d.nu == 5;
+  for (int k = 0; k < N; ++k) {
+    const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
+    const size_t idx = (size_t)k * K + m;
+    if (BF16) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(z.x, z.y), b = __floats2bfloat162_rn(z.z, z.w);
+      uint2 w;
+      w.x = *reinterpret_cast<uint32_t*>(&a);
+      w.y = *reinterpret_cast<uint32_t*>(&b);
+      d.Zb[idx] = w;
+    } else {
+      d.Z4[idx] = z;
+    }
+    if (five) {
+      const float4 z5 = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 1u);
+      if (BF16)
+        d.Z5b[idx] = __float2bfloat16_rn(z5.x);
+      else
+        d.Z5[idx] = z5.x;
+    }
+  }
+}
+
+template <int BF16>
+__device__ __forceinline__ void load_noise(const SolveDesc& d, size_t idx, float z[kNU], bool five) {
+  if (BF16) {
+    const uint2 w = __ldg(d.Zb + idx);
+    __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
+    __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    z[0] = fa.x; z[1] = fa.y; z[2] = fb.x; z[3] = fb.y;
+    z[4] = five ? __bfloat162float(d.Z5b[idx]) : 0.f;
+  } else {
+    const float4 v = __ldg(d.Z4 + idx);
+    z[0] = v.x; z[1] = v.y; z[2] = v.z; z[3] = v.w;
+    z[4] = five ? __ldg(d.Z5 + idx) : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// flash-softmax merge of partials (Eq. 4 / Eq. 5 in split form):
+//   m = min m_i, s_i = exp(-(m_i - m) / lambda), S = sum S_i s_i,
+//   P = sum P_i s_i  (P in float hi/lo pairs, compensated products)
+// ---------------------------------------------------------------------------
+struct MergeIn {
+  const double* m;   // [n]
+  const double* S;   // [n]
+  const double* P;   // [n][NNU] (float2 hi/lo or double)
+};
+
+__device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int NNU, double* out_m, double* out_S,
+                               double* out_P, double* scale_s, double* red, int f64) {
+  double mloc = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mloc = fmin(mloc, __ldcg(in.m + i));
+  const double mm = block_min_d(mloc, red);
+  double sloc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double mi = __ldcg(in.m + i);
+    const double s = (isinf(mm) || isinf(mi)) ? 0.0 : exp(-(mi - mm) * (double)d.inv_lambda);
+    scale_s[i] = s;
+    sloc += __ldcg(in.S + i) * s;
+  }
+  const double SS = block_sum_d(sloc, red);  // ends with __syncthreads: scale_s visible
+  for (int o = threadIdx.x; o < NNU; o += blockDim.x) {
+    if (f64) {
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) acc = fma(__ldcg(in.P + (size_t)i * NNU + o), scale_s[i], acc);
+      out_P[o] = acc;
+    } else {
+      float hi = 0.f, lo = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const double raw = __ldcg(in.P + (size_t)i * NNU + o);
+        const float2 v = *reinterpret_cast<const float2*>(&raw);
+        const float s = (float)scale_s[i];
+        // TwoProd(v.x, s) and TwoSum into (hi, lo)
+        const float p = v.x * s;
+        const float pe = fmaf(v.x, s, -p);
+        float t, e;
+        two_sum(hi, p, t, e);
+        hi = t;
+        lo += e + pe + v.y * s;
+      }
+      float t, e;
+      two_sum(hi, lo, t, e);
+      float2 r = make_float2(t, e);
+      out_P[o] = *reinterpret_cast<double*>(&r);
+    }
+  }
+  if (threadIdx.x == 0) {
+    *out_m = mm;
+    *out_S = SS;
+  }
+}
+
+__device__ __forceinline__ double part_value(double raw, int f64) {
+  if (f64) return raw;
+  const float2 v = *reinterpret_cast<const float2*>(&raw);
+  return (double)v.x + (double)v.y;
+}
+
+// ---------------------------------------------------------------------------
+// K2: rollout + cost + per-block weights + merge (last block)
+// ---------------------------------------------------------------------------
+template <int OBJ, int BF16>
+__global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __restrict__ descs,
+                                                            const Tile* __restrict__ tiles, LaunchIO io) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) SolveDesc sd;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ double red[32];
+  __shared__ float x0s[kNX];
+  __shared__ int s_adv, s_last, s_group_last, s_bad;
+  __shared__ double s_theta0, s_m, s_S;
+  __shared__ float s_vth0, s_f0;
+  __shared__ int s_j0;
+  __shared__ float s_best_d[32];
+  __shared__ int s_best_j[32];
+  __shared__ float s_best_t[32];
+
+  const Tile tile = tiles[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  {
+    const int* src = reinterpret_cast<const int*>(descs + tile.solve);
+    int* dst = reinterpret_cast<int*>(&sd);
+    for (int i = tid; i < (int)(sizeof(SolveDesc) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  if (tid < kNX) x0s[tid] = io.x0 ? io.x0[(size_t)tile.solve * kNX + tid] : io.x0v[tid];
+  __syncthreads();
+  const SolveDesc& d = sd;
+  const int K = d.K, N = d.N, nu = d.nu, B = d.block;
+  const int path_smem = path_fits_smem(d.S);
+  const SmemLayout Ls = smem_layout(N, OBJ, d.S, B, max(d.n_tiles, 32), path_smem);
+  float* sU = reinterpret_cast<float*>(smem + Ls.off_U);
+  int* sPrev = reinterpret_cast<int*>(smem + Ls.off_prev);
+  GateF* sG = reinterpret_cast<GateF*>(smem + Ls.off_gates);
+  float* sPath = path_smem ? reinterpret_cast<float*>(smem + Ls.off_path) : nullptr;
+  float* sX = reinterpret_cast<float*>(smem + Ls.off_xref);
+  float* sE = reinterpret_cast<float*>(smem + Ls.off_e);
+  double* sMerge = reinterpret_cast<double*>(smem + Ls.off_merge);
+  const float* path = path_smem ? sPath : d.path;
+
+  // ---- prologue: TMA bulk copies of the nominal and the path table ----
+  const uint32_t bytes_U = align16((uint32_t)N * kNU * 4u);
+  const uint32_t bytes_path = (OBJ == MPPI_OBJ_CONTOUR && path_smem) ? align16((uint32_t)d.S * 24u) : 0u;
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    s_bad = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&mbar, bytes_U + bytes_path);
+    bulk_g2s(sU, d.U, bytes_U, &mbar);
+    if (bytes_path) bulk_g2s(sPath, d.path, bytes_path, &mbar);
+  }
+  DevState* st = d.st;
+  // gate frames (computed here from the raw table: centre, yaw, half sizes)
+  if (OBJ == MPPI_OBJ_GATE) {
+    for (int i = tid; i < d.n_gates; i += blockDim.x) {
+      const float* g = d.gates + 6 * i;
+      float s, c;
+      sincosf(g[3], &s, &c);
+      sG[i] = GateF{g[0], g[1], g[2], c, s, g[4], g[5], 0.f};
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // the plant's own pass of the current gate since the last solve
+      int adv = 0;
+      if (st->has_prev && !(d.closed == 0 && st->gate >= d.n_gates)) {
+        const GateF g = sG[gate_slot(st->gate, d.n_gates, d.closed)];
+        const float* p0 = st->prev_x0;
+        const float sa = plane_dist(g, p0[0], p0[1]), sb = plane_dist(g, x0s[0], x0s[1]);
+        if (sa < 0.f && sb >= 0.f &&
+            through_opening(g, sa, sb, p0[0], p0[1], p0[2], x0s[0] - p0[0], x0s[1] - p0[1], x0s[2] - p0[2]))
+          adv = 1;
+      }
+      s_adv = adv;
+    }
+    __syncthreads();
+    for (int k = tid; k < N; k += blockDim.x) sPrev[k] = max(0, d.prevcnt[k] - s_adv);
+  }
+  double t0 = 0.0;
+  if (OBJ == MPPI_OBJ_TRACK) {
+    t0 = io.t0 ? io.t0[tile.solve] : io.t0v;
+    // reference window x_ref(t0 + k dt), k = 0..N (linear, nlerp for q)
+    const double period = (double)d.T * (double)d.dt_ref;
+    for (int k = tid; k <= N; k += blockDim.x) {
+      double tau = fmod(t0 + (double)k * (double)d.dt, period);
+      if (tau < 0) tau += period;
+      const double sidx = tau / (double)d.dt_ref;
+      int i = (int)floor(sidx);
+      float f = (float)(sidx - (double)i);
+      if (i >= d.T) { i = d.T - 1; f = 1.f; }
+      const int i1 = (i + 1) % d.T;
+      const float* a = d.ref + (size_t)13 * i;
+      const float* b = d.ref + (size_t)13 * i1;
+      float* o = sX + (size_t)13 * k;
+      for (int c = 0; c < 13; ++c) o[c] = (1.f - f) * a[c] + f * b[c];
+      const float dot = a[6] * b[6] + a[7] * b[7] + a[8] * b[8] + a[9] * b[9];
+      const float sg = dot < 0.f ? -1.f : 1.f;
+      float n2 = 0.f;
+      for (int c = 6; c < 10; ++c) {
+        o[c] = (1.f - f) * a[c] + f * sg * b[c];
+        n2 += o[c] * o[c];
+      }
+      const float rn = 1.0f / sqrtf(n2);
+      for (int c = 6; c < 10; ++c) o[c] *= rn;
+    }
+  }
+  // ---- wait for the bulk copies (bounded) ----
+  if (!mbar_wait(&mbar, 0, 200000000ull)) {
+    if (tid == 0) { s_bad = 1; atomicAdd(&st->timeouts, 1); }
+    mbar_wait(&mbar, 0, 200000000ull);
+  }
+  __syncthreads();
+  if (OBJ == MPPI_OBJ_CONTOUR) {
+    // theta_0: closest point of the path to x0 among the node segments of the
+    // window [theta_prev - back, theta_prev + ahead] (whole path on the first solve)
+    const double dsd = (double)d.L / (double)d.S;
+    int jlo = 0, jhi = d.S - 1;
+    if (st->has_theta) {
+      jlo = (int)floor((st->theta - (double)d.theta_back) / dsd);
+      jhi = (int)floor((st->theta + (double)d.theta_ahead) / dsd);
+    }
+    float best = INFINITY, bt = 0.f;
+    int bj = 0x7fffffff;
+    for (int jj = jlo + tid; jj <= jhi; jj += blockDim.x) {
+      int j = jj % d.S;
+      if (j < 0) j += d.S;
+      const int j1 = (j + 1) % d.S;
+      const float* a = path + 6 * j;
+      const float* b = path + 6 * j1;
+      const float dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+      const float rx = x0s[0] - a[0], ry = x0s[1] - a[1], rz = x0s[2] - a[2];
+      float t = (rx * dx + ry * dy + rz * dz) / (dx * dx + dy * dy + dz * dz);
+      t = clampf(t, 0.f, 1.f);
+      const float ex = rx - t * dx, ey = ry - t * dy, ez = rz - t * dz;
+      const float dist = ex * ex + ey * ey + ez * ez;
+      if (dist < best || (dist == best && jj < bj)) { best = dist; bj = jj; bt = t; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      const float ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      if (od < best || (od == best && oj < bj)) { best = od; bj = oj; bt = ot; }
+    }
+    if (lane == 0) { s_best_d[wid] = best; s_best_j[wid] = bj; s_best_t[wid] = bt; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < nw; ++w)
+        if (s_best_d[w] < best || (s_best_d[w] == best && s_best_j[w] < bj)) {
+          best = s_best_d[w]; bj = s_best_j[w]; bt = s_best_t[w];
+        }
+      int j = bj % d.S;
+      if (j < 0) j += d.S;
+      s_j0 = j;
+      s_f0 = bt * d.ds;  // metres past node j0
+      double th = ((double)j + (double)bt) * dsd;
+      s_theta0 = th;
+      s_vth0 = st->has_theta ? (float)st->v_theta : 0.f;
+    }
+    __syncthreads();
+  }
+  if (tile.m0 == 0 && OBJ == MPPI_OBJ_TRACK) {
+    for (int i = tid; i < (N + 1) * kNX; i += blockDim.x) d.xref[i] = sX[i];
+  }
+
+  // ---- the rollout: one sample per thread ----
+  const int m = tile.m0 + tid;
+  const bool active = tid < B && m < K && !s_bad;
+  const bool five = nu == 5;
+  ModelRegs M;
+  M.inv_mass = d.inv_mass; M.gravity = d.gravity; M.k_omega = d.k_omega;
+  M.g0 = d.gyro[0]; M.g1 = d.gyro[1]; M.g2 = d.gyro[2];
+  M.d0 = d.drag[0]; M.d1 = d.drag[1]; M.d2 = d.drag[2]; M.has_drag = d.has_drag;
+  float Jh = 0.f, Jc = 0.f;
+  int passed = 0, first = -1;
+  if (active) {
+    Quad s;
+    s.px = x0s[0]; s.py = x0s[1]; s.pz = x0s[2];
+    s.cpx = s.cpy = s.cpz = 0.f;
+    s.vx = x0s[3]; s.vy = x0s[4]; s.vz = x0s[5];
+    s.cvx = s.cvy = s.cvz = 0.f;
+    s.qw = x0s[6]; s.qx = x0s[7]; s.qy = x0s[8]; s.qz = x0s[9];
+    s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
+    const float h = d.dt;
+    // objective state
+    int gi = 0;
+    GateF g, g0;
+    float sa = 0.f;
+    if (OBJ == MPPI_OBJ_GATE) {
+      gi = st->gate + s_adv;
+      g = sG[gate_slot(gi, d.n_gates, d.closed)];
+      g0 = g;
+      sa = plane_dist(g, s.px, s.py);
+    }
+    int node = 0;
+    float frac_m = 0.f, frac_c = 0.f, vth = 0.f, c_prev = 0.f;
+    if (OBJ == MPPI_OBJ_CONTOUR) {
+      node = s_j0;
+      frac_m = s_f0;
+      vth = s_vth0;
+      c_prev = st->has_prev ? st->c_last : d.hover;
+    }
+    float z[kNU];
+    for (int k = 0; k < N; ++k) {
+      load_noise<BF16>(d, (size_t)k * K + m, z, five);
+      const float* Uk = sU + kNU * k;
+      const float u0 = clampf(Uk[0] + d.sigma[0] * z[0], d.u_min[0], d.u_max[0]);
+      const float u1 = clampf(Uk[1] + d.sigma[1] * z[1], d.u_min[1], d.u_max[1]);
+      const float u2 = clampf(Uk[2] + d.sigma[2] * z[2], d.u_min[2], d.u_max[2]);
+      const float u3 = clampf(Uk[3] + d.sigma[3] * z[3], d.u_min[3], d.u_max[3]);
+      float stage = 0.f;
+      if (OBJ == MPPI_OBJ_TRACK) {
+        // Eq. 8 stage term on x_k and u_k
+        const float* xr = sX + kNX * k;
+        const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
+        const float sg = dot < 0.f ? -1.f : 1.f;
+        float e;
+        e = pxt(s) - xr[0]; stage += d.Q[0] * e * e;
+        e = pyt(s) - xr[1]; stage += d.Q[1] * e * e;
+        e = pzt(s) - xr[2]; stage += d.Q[2] * e * e;
+        e = (s.vx - s.cvx) - xr[3]; stage += d.Q[3] * e * e;
+        e = (s.vy - s.cvy) - xr[4]; stage += d.Q[4] * e * e;
+        e = (s.vz - s.cvz) - xr[5]; stage += d.Q[5] * e * e;
+        e = s.qw - sg * xr[6]; stage += d.Q[6] * e * e;
+        e = s.qx - sg * xr[7]; stage += d.Q[7] * e * e;
+        e = s.qy - sg * xr[8]; stage += d.Q[8] * e * e;
+        e = s.qz - sg * xr[9]; stage += d.Q[9] * e * e;
+        e = s.wx - xr[10]; stage += d.Q[10] * e * e;
+        e = s.wy - xr[11]; stage += d.Q[11] * e * e;
+        e = s.wz - xr[12]; stage += d.Q[12] * e * e;
+        const float du = u0 - d.hover;
+        stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
+      }
+      // positions at the start of the step (compensated)
+      const float ax = pxt(s), ay = pyt(s), az = pzt(s);
+      float dpx, dpy, dpz;
+      rk4_step(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+      const float bx = pxt(s), by = pyt(s), bz = pzt(s);
+      if (OBJ == MPPI_OBJ_GATE) {
+        // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g)
+        const float prog = dpx * ((ax - g.cx) + (bx - g.cx)) + dpy * ((ay - g.cy) + (by - g.cy)) +
+                           dpz * ((az - g.cz) + (bz - g.cz));
+        const float ex = ax - g0.cx, ey = ay - g0.cy, ez = az - g0.cz;
+        const float d0 = ex * ex + ey * ey + ez * ez;
+        stage = prog + (d0 < d.r_near2 ? d.q_near * d0 : 0.f);
+        const float sb = plane_dist(g, bx, by);
+        if (sa < 0.f && sb >= 0.f) {
+          const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
+          const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
+          if (!open_track_done && ok_time && through_opening(g, sa, sb, ax, ay, az, bx - ax, by - ay, bz - az)) {
+            ++passed;
+            ++gi;
+            if (first < 0) first = k;
+            g = sG[gate_slot(gi, d.n_gates, d.closed)];
+            sa = plane_dist(g, bx, by);
+          } else {
+            sa = sb;
+          }
+        } else {
+          sa = sb;
+        }
+      } else if (OBJ == MPPI_OBJ_CONTOUR) {
+        // Eq. 9 with the progress state (theta, v_theta), terms on x_{k+1}
+        const float a = clampf(Uk[4] + d.sigma[4] * z[4], d.u_min[4], d.u_max[4]);
+        const float v1 = clampf(vth + a * h, 0.f, d.v_theta_max);
+        kahan_add(frac_m, frac_c, 0.5f * (vth + v1) * h);
+        float fm = frac_m - frac_c;
+        while (fm >= d.ds) {
+          frac_m -= d.ds;
+          fm = frac_m - frac_c;
+          if (++node >= d.S) node -= d.S;
+        }
+        const float fr = fm * d.inv_ds;
+        const int n1 = node + 1 >= d.S ? 0 : node + 1;
+        const float* A = path + 6 * node;
+        const float* Bn = path + 6 * n1;
+        const float Px = A[0] + fr * (Bn[0] - A[0]), Py = A[1] + fr * (Bn[1] - A[1]),
+                    Pz = A[2] + fr * (Bn[2] - A[2]);
+        float Tx = A[3] + fr * (Bn[3] - A[3]), Ty = A[4] + fr * (Bn[4] - A[4]), Tz = A[5] + fr * (Bn[5] - A[5]);
+        const float rn = rsqrtf(Tx * Tx + Ty * Ty + Tz * Tz);
+        Tx *= rn; Ty *= rn; Tz *= rn;
+        const float ex = bx - Px, ey = by - Py, ez = bz - Pz;
+        const float et = ex * Tx + ey * Ty + ez * Tz;
+        const float cx = ex - et * Tx, cy = ey - et * Ty, cz = ez - et * Tz;
+        const float dT = u0 - c_prev;
+        stage = d.q_lag * et * et + d.q_cont * (cx * cx + cy * cy + cz * cz) +
+                d.q_omega[0] * s.wx * s.wx + d.q_omega[1] * s.wy * s.wy + d.q_omega[2] * s.wz * s.wz +
+                d.r_dv * a * a + d.r_dthrust * dT * dT - d.mu * v1;
+        c_prev = u0;
+        vth = v1;
+      } else {
+        if (k == N - 1) {
+          const float* xr = sX + kNX * N;
+          const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
+          const float sg = dot < 0.f ? -1.f : 1.f;
+          float e;
+          e = bx - xr[0]; stage += d.QN[0] * e * e;
+          e = by - xr[1]; stage += d.QN[1] * e * e;
+          e = bz - xr[2]; stage += d.QN[2] * e * e;
+          e = (s.vx - s.cvx) - xr[3]; stage += d.QN[3] * e * e;
+          e = (s.vy - s.cvy) - xr[4]; stage += d.QN[4] * e * e;
+          e = (s.vz - s.cvz) - xr[5]; stage += d.QN[5] * e * e;
+          e = s.qw - sg * xr[6]; stage += d.QN[6] * e * e;
+          e = s.qx - sg * xr[7]; stage += d.QN[7] * e * e;
+          e = s.qy - sg * xr[8]; stage += d.QN[8] * e * e;
+          e = s.qz - sg * xr[9]; stage += d.QN[9] * e * e;
+          e = s.wx - xr[10]; stage += d.QN[10] * e * e;
+          e = s.wy - xr[11]; stage += d.QN[11] * e * e;
+          e = s.wz - xr[12]; stage += d.QN[12] * e * e;
+        }
+      }
+      stage += limit_penalty(d.w_limit, d.omega_max, d.z_floor, s);
+      kahan_add(Jh, Jc, stage);
+    }
+  }
+
+  // ---- per-sample outputs and the block's share of Eq. 4 ----
+  const double Jd = (double)Jh - (double)Jc;
+  const bool valid = active && isfinite(Jd);
+  if (active) {
+    d.J[m] = Jd;
+    d.info[m] = passed | ((first + 1) << 16);
+  }
+  const double m_t = block_min_d(valid ? Jd : INFINITY, red);
+  float e = 0.f;
+  if (valid && !isinf(m_t)) e = expf(-(float)(Jd - m_t) * d.inv_lambda);
+  if (tid < B) sE[tid] = e;
+  const double S_t = block_sum_d((double)e, red);  // also publishes sE
+
+  // ---- weighted deviation sums per (step, input) of this tile (Eq. 5) ----
+  const int nvalid = min(B, K - tile.m0);
+  const int NNU = N * kNU;
+  const int tile_in_solve = tile.m0 / B;
+  double* myP = d.part_P + (size_t)tile_in_solve * NNU;
+  const int acc = d.accum;
+  for (int k = wid; k < N; k += nw) {
+    const float* Uk = sU + kNU * k;
+    float hi[kNU], lo[kNU];
+    double dacc[kNU];
+#pragma unroll
+    for (int j = 0; j < kNU; ++j) { hi[j] = 0.f; lo[j] = 0.f; dacc[j] = 0.0; }
+    for (int i = lane; i < nvalid; i += 32) {
+      const float w = sE[i];
+      float zz[kNU];
+      load_noise<BF16>(d, (size_t)k * K + tile.m0 + i, zz, five);
+#pragma unroll
+      for (int j = 0; j < kNU; ++j) {
+        if (j >= nu) break;
+        const float u = clampf(Uk[j] + d.sigma[j] * zz[j], d.u_min[j], d.u_max[j]);
+        const float dv = u - Uk[j];
+        if (acc == MPPI_ACC_F64) {
+          dacc[j] = fma((double)w, (double)dv, dacc[j]);
+        } else if (acc == MPPI_ACC_F32) {
+          hi[j] = fmaf(w, dv, hi[j]);
+        } else {
+          kahan_add(hi[j], lo[j], w * dv);
+        }
+      }
+    }
+    // cross-lane reduction, fixed order
+#pragma unroll
+    for (int j = 0; j < kNU; ++j) {
+      if (j >= nu) break;
+      if (acc == MPPI_ACC_F64) {
+        double v = dacc[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) myP[kNU * k + j] = v;
+      } else if (acc == MPPI_ACC_F32) {
+        float v = hi[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+          float2 r = make_float2(v, 0.f);
+          myP[kNU * k + j] = *reinterpret_cast<double*>(&r);
+        }
+      } else {
+        float h1 = hi[j], l1 = -lo[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, h1, o), l2 = __shfl_xor_sync(0xffffffffu, l1, o);
+          float s_, e_;
+          two_sum(h1, h2, s_, e_);
+          const float l = e_ + l1 + l2;
+          two_sum(s_, l, h1, l1);
+        }
+        if (lane == 0) {
+          float2 r = make_float2(h1, l1);
+          myP[kNU * k + j] = *reinterpret_cast<double*>(&r);
+        }
+      }
+    }
+    if (lane == 0)
+      for (int j = nu; j < kNU; ++j) {
+        float2 r = make_float2(0.f, 0.f);
+        myP[kNU * k + j] = acc == MPPI_ACC_F64 ? 0.0 : *reinterpret_cast<double*>(&r);
+      }
+  }
+  if (tid == 0) {
+    d.part_m[tile_in_solve] = m_t;
+    d.part_S[tile_in_solve] = S_t;
+  }
+
+  // ---- two-level merge: last block of each group, then last group ----
+  const int T = d.n_tiles;
+  const int G = group_size_for(T);
+  const int n_groups = (T + G - 1) / G;
+  const int grp = tile_in_solve / G;
+  const int gsize = min(G, T - grp * G);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t c = atomicAdd(d.ticket + 1 + grp, 1u);
+    s_group_last = (c == (uint32_t)gsize - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_group_last) return;
+  __threadfence();
+  const int f64 = acc == MPPI_ACC_F64;
+  double* gm = d.part_m + T;
+  double* gS = d.part_S + T;
+  double* gP = d.part_P + (size_t)T * NNU;
+  if (n_groups > 1) {
+    MergeIn in{d.part_m + grp * G, d.part_S + grp * G, d.part_P + (size_t)grp * G * NNU};
+    merge_partials(d, in, gsize, NNU, gm + grp, gS + grp, gP + (size_t)grp * NNU, sMerge, red, f64);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      d.ticket[1 + grp] = 0u;
+      const uint32_t c = atomicAdd(d.ticket, 1u);
+      s_last = (c == (uint32_t)n_groups - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+  } else if (tid == 0) {
+    d.ticket[1 + grp] = 0u;
+  }
+  // final merge -> U*_new = U* + P / S
+  {
+    MergeIn in;
+    int n;
+    if (n_groups > 1) {
+      in = MergeIn{gm, gS, gP};
+      n = n_groups;
+    } else {
+      in = MergeIn{d.part_m, d.part_S, d.part_P};
+      n = T;
+    }
+    double* fP = gP + (size_t)n_groups * NNU;  // scratch row for the final sums
+    merge_partials(d, in, n, NNU, &s_m, &s_S, fP, sMerge, red, f64);
+    __threadfence_block();
+    __syncthreads();
+    const bool degenerate = isinf(s_m) || !(s_S > 0.0);
+    float* u0o = io.u0 + (size_t)tile.solve * kNU;
+    for (int o = tid; o < NNU; o += blockDim.x) {
+      const int k = o / kNU, j = o - k * kNU;
+      float v = sU[o];
+      if (!degenerate && j < nu) v = (float)((double)sU[o] + part_value(fP[o], f64) / s_S);
+      if (j >= nu) v = 0.f;
+      d.unew[o] = v;
+      if (k == 0) u0o[j] = v;
+    }
+    __syncthreads();
+    __threadfence();
+    // warm start: shift by one, repeat the last row over the whole capacity
+    for (int o = tid; o < d.N_cap * kNU; o += blockDim.x) {
+      const int k = o / kNU, j = o - k * kNU;
+      const int src = min(k + 1, N - 1);
+      d.U[o] = d.unew[src * kNU + j];
+    }
+    if (tid < kNX) st->prev_x0[tid] = x0s[tid];
+    if (tid == 0) {
+      const float c0 = d.unew[0];
+      st->gate0 = st->gate + (OBJ == MPPI_OBJ_GATE ? s_adv : 0);
+      st->adv = OBJ == MPPI_OBJ_GATE ? s_adv : 0;
+      st->gate = st->gate0;
+      st->status = degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
+      st->iter += 1u;
+      st->has_prev = 1;
+      st->n_nom = N;
+      st->c_last = c0;
+      if (OBJ == MPPI_OBJ_CONTOUR) {
+        const float a0 = d.unew[4];
+        st->theta = s_theta0;
+        st->v_theta = (double)clampf(s_vth0 + a0 * d.dt, 0.f, d.v_theta_max);
+        st->has_theta = 1;
+        st->scal[0] = s_theta0;
+        st->scal[1] = (double)s_vth0;
+      }
+      st->scal[2] = s_m;
+      st->scal[3] = s_S;
+      if (io.status) io.status[tile.solve] = degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
+      d.ticket[0] = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: nominal rollout (gate pass counts for the temporal rule of the next solve)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restrict__ descs,
+                                                      const int32_t* __restrict__ which, int n) {
+  __shared__ int sPrev[4][kMaxN];
+  __shared__ GateF sG[4][kMaxGates];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 4 + w;
+  if (i >= n) return;
+  const SolveDesc& d = descs[which[i]];
+  DevState* st = d.st;
+  const int N = d.N;
+  const int adv = st->adv;
+  for (int k = lane; k < N; k += 32) sPrev[w][k] = max(0, d.prevcnt[k] - adv);
+  for (int g = lane; g < d.n_gates; g += 32) {
+    const float* gr = d.gates + 6 * g;
+    float s, c;
+    sincosf(gr[3], &s, &c);
+    sG[w][g] = GateF{gr[0], gr[1], gr[2], c, s, gr[4], gr[5], 0.f};
+  }
+  __syncwarp();
+  int pc_last = 0;
+  if (lane == 0) {
+    ModelRegs M;
+    M.inv_mass = d.inv_mass; M.gravity = d.gravity; M.k_omega = d.k_omega;
+    M.g0 = d.gyro[0]; M.g1 = d.gyro[1]; M.g2 = d.gyro[2];
+    M.d0 = d.drag[0]; M.d1 = d.drag[1]; M.d2 = d.drag[2]; M.has_drag = d.has_drag;
+    const float* x0 = st->prev_x0;
+    Quad s;
+    s.px = x0[0]; s.py = x0[1]; s.pz = x0[2]; s.cpx = s.cpy = s.cpz = 0.f;
+    s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5]; s.cvx = s.cvy = s.cvz = 0.f;
+    s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
+    s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
+    int gi = st->gate, passed = 0;
+    GateF g = sG[w][gate_slot(gi, d.n_gates, d.closed)];
+    float sa = plane_dist(g, s.px, s.py);
+    d.passcnt[0] = 0;
+    for (int k = 0; k < N; ++k) {
+      const float* u = d.unew + kNU * k;
+      const float ax = pxt(s), ay = pyt(s), az = pzt(s);
+      float dpx, dpy, dpz;
+      rk4_step(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+      const float bx = pxt(s), by = pyt(s), bz = pzt(s);
+      const float sb = plane_dist(g, bx, by);
+      if (sa < 0.f && sb >= 0.f) {
+        const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
+        const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[w][k] <= passed;
+        if (!open_track_done && ok_time && through_opening(g, sa, sb, ax, ay, az, bx - ax, by - ay, bz - az)) {
+          ++passed;
+          ++gi;
+          g = sG[w][gate_slot(gi, d.n_gates, d.closed)];
+          sa = plane_dist(g, bx, by);
+        } else {
+          sa = sb;
+        }
+      } else {
+        sa = sb;
+      }
+      d.passcnt[k + 1] = passed;
+    }
+    pc_last = passed;
+  }
+  __syncwarp();
+  pc_last = __shfl_sync(0xffffffffu, pc_last, 0);
+  // counts as seen from the next solve (time aligned: one step later)
+  const int shift = d.temporal_rule == MPPI_RULE_SAME_INDEX ? 0 : 1;
+  for (int k = lane; k < d.N_cap; k += 32) {
+    const int src = k + shift;
+    d.prevcnt[k] = src <= N ? d.passcnt[src] : pc_last;
+  }
+  if (lane == 0) st->n_prev = N;
+}
+
+// ---------------------------------------------------------------------------
+// test entry kernels
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
+                              uint32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 x = philox4x32_10(make_uint4(c0 + (uint32_t)i, c1, c2, c3), k0, k1);
+  reinterpret_cast<uint4*>(out)[i] = x;
+}
+
+__global__ void normals_kernel(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int n,
+                               float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  reinterpret_cast<float4*>(out)[i] = normals4(seed, drone, (uint32_t)i, k, it, blk);
+}
+
+__global__ void rollout_states_kernel(ModelRegs M, float dt, int N, int B, const float* __restrict__ x0,
+                                      const float* __restrict__ U, float* __restrict__ X) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  Quad s;
+  s.px = x0[0]; s.py = x0[1]; s.pz = x0[2]; s.cpx = s.cpy = s.cpz = 0.f;
+  s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5]; s.cvx = s.cvy = s.cvz = 0.f;
+  s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
+  s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
+  float* o = X + (size_t)b * (N + 1) * kNX;
+  for (int c = 0; c < kNX; ++c) o[c] = x0[c];
+  for (int k = 0; k < N; ++k) {
+    const float* u = U + ((size_t)b * N + k) * 4;
+    float dpx, dpy, dpz;
+    rk4_step(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+    float* r = o + (size_t)(k + 1) * kNX;
+    r[0] = pxt(s); r[1] = pyt(s); r[2] = pzt(s);
+    r[3] = s.vx - s.cvx; r[4] = s.vy - s.cvy; r[5] = s.vz - s.cvz;
+    r[6] = s.qw; r[7] = s.qx; r[8] = s.qy; r[9] = s.qz;
+    r[10] = s.wx; r[11] = s.wy; r[12] = s.wz;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers
+// ---------------------------------------------------------------------------
+static unsigned long long g_launches = 0;
+unsigned long long launches_so_far() { return g_launches; }
+
+cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
+                         cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  if (bf16)
+    noise_kernel<1><<<n_tiles, block, 0, s>>>(descs, tiles);
+  else
+    noise_kernel<0><<<n_tiles, block, 0, s>>>(descs, tiles);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <int OBJ, int BF16>
+static cudaError_t configure_t() {
+  return cudaFuncSetAttribute(rollout_kernel<OBJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t configure_kernels() {
+  cudaError_t e;
+  if ((e = configure_t<MPPI_OBJ_GATE, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_GATE, 1>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_CONTOUR, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_CONTOUR, 1>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_TRACK, 0>()) != cudaSuccess) return e;
+  return configure_t<MPPI_OBJ_TRACK, 1>();
+}
+
+template <int OBJ, int BF16>
+static cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
+                                    uint32_t smem, LaunchIO io, cudaStream_t s) {
+  rollout_kernel<OBJ, BF16><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
+                           int block, uint32_t smem, LaunchIO io, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  switch (objective * 2 + (bf16 ? 1 : 0)) {
+    case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0>(descs, tiles, n_tiles, block, smem, io, s);
+    case 1: return launch_rollout_t<MPPI_OBJ_GATE, 1>(descs, tiles, n_tiles, block, smem, io, s);
+    case 2: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0>(descs, tiles, n_tiles, block, smem, io, s);
+    case 3: return launch_rollout_t<MPPI_OBJ_CONTOUR, 1>(descs, tiles, n_tiles, block, smem, io, s);
+    case 4: return launch_rollout_t<MPPI_OBJ_TRACK, 0>(descs, tiles, n_tiles, block, smem, io, s);
+    case 5: return launch_rollout_t<MPPI_OBJ_TRACK, 1>(descs, tiles, n_tiles, block, smem, io, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  nominal_kernel<<<(n + 3) / 4, 128, 0, s>>>(descs, which, n);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
+                          uint32_t* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  philox_kernel<<<(n + 127) / 128, 128, 0, s>>>(k0, k1, c0, c1, c2, c3, n, out);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int n, float* out,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  normals_kernel<<<(n + 127) / 128, 128, 0, s>>>(seed, drone, k, it, blk, n, out);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_states(const SolveDesc& md, float dt, int N, int B, const float* x0, const float* U,
+                                  float* X, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  ModelRegs M;
+  M.inv_mass = md.inv_mass; M.gravity = md.gravity; M.k_omega = md.k_omega;
+  M.g0 = md.gyro[0]; M.g1 = md.gyro[1]; M.g2 = md.gyro[2];
+  M.d0 = md.drag[0]; M.d1 = md.drag[1]; M.d2 = md.drag[2]; M.has_drag = md.has_drag;
+  rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, dt, N, B, x0, U, X);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace mppi

@@ -1,0 +1,40 @@
+// mppi_launch.h -- host-side entry points of the kernels (internal to libmppi)
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mppi_device.cuh"
+
+namespace mppi {
+
+// partials of a solve are merged in groups of this size (two-level tree);
+// T <= 16 tiles merge in one level
+__host__ __device__ inline int group_size_for(int T) {
+  if (T <= 16) return T;
+  int g = 1;
+  while (g * g < T) ++g;
+  return g < 8 ? 8 : g;
+}
+__host__ __device__ inline int n_groups_for(int T) {
+  const int G = group_size_for(T);
+  return (T + G - 1) / G;
+}
+
+__host__ __device__ int path_fits_smem(int S);
+uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap);
+unsigned long long launches_so_far();
+// sets the dynamic shared-memory limit of every rollout kernel (once per device)
+cudaError_t configure_kernels();
+
+cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
+                         cudaStream_t s);
+cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
+                           int block, uint32_t smem, LaunchIO io, cudaStream_t s);
+cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s);
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
+                          uint32_t* out, cudaStream_t s);
+cudaError_t launch_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int n, float* out,
+                           cudaStream_t s);
+cudaError_t launch_rollout_states(const SolveDesc& model, float dt, int N, int B, const float* x0, const float* U,
+                                  float* X, cudaStream_t s);
+
+}  // namespace mppi

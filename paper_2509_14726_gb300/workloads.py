@@ -113,6 +113,25 @@ class Track:
                      r(self.ref), float(np.float32(self.dt_ref)))
 
 
+def _r32(v):
+    if isinstance(v, (tuple, list)):
+        return tuple(float(np.float32(x)) for x in v)
+    if isinstance(v, float):
+        return float(np.float32(v))
+    return v
+
+
+def f32_model(mc: ModelConfig) -> ModelConfig:
+    """The same model with every real parameter rounded to binary32 (what the
+    CUDA path receives)."""
+    return ModelConfig(**{f.name: _r32(getattr(mc, f.name)) for f in dataclasses.fields(mc)})
+
+
+def f32_solve(sc: SolveConfig) -> SolveConfig:
+    """The same solve parameters with every real value rounded to binary32."""
+    return SolveConfig(**{f.name: _r32(getattr(sc, f.name)) for f in dataclasses.fields(sc)})
+
+
 # --------------------------------------------------------------------------
 # gates
 # --------------------------------------------------------------------------
