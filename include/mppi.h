@@ -176,6 +176,15 @@ int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s
                            float* d_u0s);
 int mppi_batch_destroy(mppi_batch b);
 
+/* Tracing: runs the plan's launch sequence n_iters times WITHOUT the graph on
+ * `stream`, with CUDA events between the phases, on the device-resident
+ * inputs of the last mppi_batch_solve (or zeros).  Writes the mean duration
+ * per iteration in ms of: [0] noise kernels, [1] rollout kernel of the gate
+ * objective, [2] contouring, [3] tracking, [4] nominal rollout, [5] total.
+ * Phases without work report 0.  Advances every handle's state n_iters
+ * times, like n_iters solves. */
+int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out[6]);
+
 /* Changes K and/or N of an existing handle (within K_cap / N_cap).  The
  * nominal keeps its first rows (the last row repeats when N grows). */
 int mppi_set_shape(mppi_handle h, int32_t K, int32_t N);

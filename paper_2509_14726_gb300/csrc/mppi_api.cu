@@ -151,6 +151,7 @@ struct mppi_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev = nullptr;
+  int kernels_per_solve = 0;  // kernels one launch of the sequence runs
 };
 
 namespace {
@@ -346,22 +347,22 @@ int mppi_default_params(mppi_params_t* p, int32_t objective, int32_t K, int32_t 
   p->q_near = 0.3f;
   p->r_near = 1.5f;
   p->temporal_rule = MPPI_RULE_TIME_ALIGNED;
-  p->q_lag = 10.f;
-  p->q_cont = 100.f;
-  for (int i = 0; i < 3; ++i) p->q_omega[i] = 0.01f;
-  p->r_dv = 0.01f;
-  p->r_dthrust = 0.01f;
-  p->mu = 1.f;
+  p->q_lag = 1.f;
+  p->q_cont = 10.f;
+  for (int i = 0; i < 3; ++i) p->q_omega[i] = 0.001f;
+  p->r_dv = 0.001f;
+  p->r_dthrust = 0.001f;
+  p->mu = 0.1f;
   p->v_theta_max = 20.f;
   p->theta_back = 2.f;
   p->theta_ahead = 10.f;
   for (int i = 0; i < 13; ++i) {
-    const float q = i < 3 ? 100.f : i < 6 ? 1.f : i < 10 ? 10.f : 0.1f;
+    const float q = i < 3 ? 10.f : i < 6 ? 0.1f : i < 10 ? 1.f : 0.01f;
     p->Q[i] = q;
     p->QN[i] = 2.f * q;
   }
-  p->R[0] = 0.01f;
-  p->R[1] = p->R[2] = p->R[3] = 0.1f;
+  p->R[0] = 0.001f;
+  p->R[1] = p->R[2] = p->R[3] = 0.01f;
   p->noise_dtype = MPPI_NOISE_F32;
   p->accum = MPPI_ACC_KAHAN32;
   p->block = 128;
@@ -878,6 +879,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->n_which = (int)which.size();
   if (!which.empty() && cudaMemcpy(b->d_which, which.data(), sizeof(int32_t) * which.size(), cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "work list upload failed"));
+  b->kernels_per_solve = (int)b->noise_groups.size() + (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
   int rc = hostio_alloc(b->io, n);
   if (rc) return cleanup(rc);
   if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
@@ -894,10 +896,12 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
     int rc2 = batch_enqueue(b, io, b->cap_stream);
-    cudaError_t e1 = cudaEventRecord(b->ev, b->cap_stream);
+    cudaError_t e1 = cudaEventRecordWithFlags(b->ev, b->cap_stream, cudaEventRecordExternal);
     cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
     cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
-    if (rc2 || e1 || e2 || e3) return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed"));
+    if (rc2 || e1 || e2 || e3)
+      return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed (%s / %s / %s)", cudaGetErrorString(e1),
+                          cudaGetErrorString(e2), cudaGetErrorString(e3)));
     if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
   }
@@ -925,6 +929,7 @@ int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* st
     memset(b->io.t0, 0, sizeof(double) * b->n);
   if (b->use_graph) {
     CU(cudaGraphLaunch(b->exec, s));
+    add_launches(b->kernels_per_solve);
   } else {
     LaunchIO io;
     memset(&io, 0, sizeof io);
@@ -942,6 +947,50 @@ int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* st
   for (int i = 0; i < b->n; ++i)
     if (((volatile int32_t*)b->io.status)[i] == MPPI_WARN_DEGENERATE)
       return fail(MPPI_WARN_DEGENERATE, "solve %d: every sample cost was non-finite", i);
+  return MPPI_OK;
+}
+
+int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out[6]) {
+  if (!b || n_iters < 1 || !ms_out) return fail(MPPI_ERR_ARG, "bad arguments");
+  int rc = batch_check(b);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LaunchIO io;
+  memset(&io, 0, sizeof io);
+  io.x0 = b->io.d_x0;
+  io.t0 = b->io.d_t0;
+  io.u0 = b->io.d_u0;
+  io.status = b->io.d_status;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) CU(cudaEventCreate(&ev[i]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  int status = MPPI_OK;
+  for (int it = 0; it < n_iters && status == MPPI_OK; ++it) {
+    cudaEventRecord(ev[0], s);
+    for (const auto& g : b->noise_groups)
+      if (launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s) != cudaSuccess) status = MPPI_ERR_CUDA;
+    cudaEventRecord(ev[1], s);
+    for (int obj = 0; obj < 3; ++obj) {
+      for (const auto& g : b->rollout_groups)
+        if (g.objective == obj &&
+            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s) != cudaSuccess)
+          status = MPPI_ERR_CUDA;
+      cudaEventRecord(ev[2 + obj], s);
+    }
+    if (launch_nominal(b->d_descs, b->d_which, b->n_which, s) != cudaSuccess) status = MPPI_ERR_CUDA;
+    cudaEventRecord(ev[5], s);
+    if (cudaEventSynchronize(ev[5]) != cudaSuccess) status = MPPI_ERR_CUDA;
+    float t;
+    cudaEventElapsedTime(&t, ev[0], ev[1]); acc[0] += t;
+    cudaEventElapsedTime(&t, ev[1], ev[2]); acc[1] += t;
+    cudaEventElapsedTime(&t, ev[2], ev[3]); acc[2] += t;
+    cudaEventElapsedTime(&t, ev[3], ev[4]); acc[3] += t;
+    cudaEventElapsedTime(&t, ev[4], ev[5]); acc[4] += t;
+    cudaEventElapsedTime(&t, ev[0], ev[5]); acc[5] += t;
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  if (status) return fail(status, "profiled launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int i = 0; i < 6; ++i) ms_out[i] = (float)(acc[i] / n_iters);
   return MPPI_OK;
 }
 

@@ -489,12 +489,12 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
         const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
         const float sg = dot < 0.f ? -1.f : 1.f;
         float e;
-        e = pxt(s) - xr[0]; stage += d.Q[0] * e * e;
-        e = pyt(s) - xr[1]; stage += d.Q[1] * e * e;
-        e = pzt(s) - xr[2]; stage += d.Q[2] * e * e;
-        e = (s.vx - s.cvx) - xr[3]; stage += d.Q[3] * e * e;
-        e = (s.vy - s.cvy) - xr[4]; stage += d.Q[4] * e * e;
-        e = (s.vz - s.cvz) - xr[5]; stage += d.Q[5] * e * e;
+        e = (s.px - xr[0]) - s.cpx; stage += d.Q[0] * e * e;
+        e = (s.py - xr[1]) - s.cpy; stage += d.Q[1] * e * e;
+        e = (s.pz - xr[2]) - s.cpz; stage += d.Q[2] * e * e;
+        e = (s.vx - xr[3]) - s.cvx; stage += d.Q[3] * e * e;
+        e = (s.vy - xr[4]) - s.cvy; stage += d.Q[4] * e * e;
+        e = (s.vz - xr[5]) - s.cvz; stage += d.Q[5] * e * e;
         e = s.qw - sg * xr[6]; stage += d.Q[6] * e * e;
         e = s.qx - sg * xr[7]; stage += d.Q[7] * e * e;
         e = s.qy - sg * xr[8]; stage += d.Q[8] * e * e;
@@ -505,16 +505,18 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
         const float du = u0 - d.hover;
         stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
       }
-      // positions at the start of the step (compensated)
-      const float ax = pxt(s), ay = pyt(s), az = pzt(s);
+      // positions at the start of the step (value and compensation kept apart)
+      const float apx = s.px, apy = s.py, apz = s.pz, acx = s.cpx, acy = s.cpy, acz = s.cpz;
+      const float ax = apx - acx, ay = apy - acy, az = apz - acz;
       float dpx, dpy, dpz;
       rk4_step(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
       const float bx = pxt(s), by = pyt(s), bz = pzt(s);
       if (OBJ == MPPI_OBJ_GATE) {
         // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g)
-        const float prog = dpx * ((ax - g.cx) + (bx - g.cx)) + dpy * ((ay - g.cy) + (by - g.cy)) +
-                           dpz * ((az - g.cz) + (bz - g.cz));
-        const float ex = ax - g0.cx, ey = ay - g0.cy, ez = az - g0.cz;
+        const float prog = dpx * ((apx - g.cx) - acx + ((s.px - g.cx) - s.cpx)) +
+                           dpy * ((apy - g.cy) - acy + ((s.py - g.cy) - s.cpy)) +
+                           dpz * ((apz - g.cz) - acz + ((s.pz - g.cz) - s.cpz));
+        const float ex = (apx - g0.cx) - acx, ey = (apy - g0.cy) - acy, ez = (apz - g0.cz) - acz;
         const float d0 = ex * ex + ey * ey + ez * ez;
         stage = prog + (d0 < d.r_near2 ? d.q_near * d0 : 0.f);
         const float sb = plane_dist(g, bx, by);
@@ -548,12 +550,13 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
         const int n1 = node + 1 >= d.S ? 0 : node + 1;
         const float* A = path + 6 * node;
         const float* Bn = path + 6 * n1;
-        const float Px = A[0] + fr * (Bn[0] - A[0]), Py = A[1] + fr * (Bn[1] - A[1]),
-                    Pz = A[2] + fr * (Bn[2] - A[2]);
+        // e = p - P(theta) with P = A + fr (B - A), formed as (p - A) - fr (B - A)
         float Tx = A[3] + fr * (Bn[3] - A[3]), Ty = A[4] + fr * (Bn[4] - A[4]), Tz = A[5] + fr * (Bn[5] - A[5]);
         const float rn = rsqrtf(Tx * Tx + Ty * Ty + Tz * Tz);
         Tx *= rn; Ty *= rn; Tz *= rn;
-        const float ex = bx - Px, ey = by - Py, ez = bz - Pz;
+        const float ex = ((s.px - A[0]) - fr * (Bn[0] - A[0])) - s.cpx;
+        const float ey = ((s.py - A[1]) - fr * (Bn[1] - A[1])) - s.cpy;
+        const float ez = ((s.pz - A[2]) - fr * (Bn[2] - A[2])) - s.cpz;
         const float et = ex * Tx + ey * Ty + ez * Tz;
         const float cx = ex - et * Tx, cy = ey - et * Ty, cz = ez - et * Tz;
         const float dT = u0 - c_prev;
@@ -568,12 +571,12 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
           const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
           const float sg = dot < 0.f ? -1.f : 1.f;
           float e;
-          e = bx - xr[0]; stage += d.QN[0] * e * e;
-          e = by - xr[1]; stage += d.QN[1] * e * e;
-          e = bz - xr[2]; stage += d.QN[2] * e * e;
-          e = (s.vx - s.cvx) - xr[3]; stage += d.QN[3] * e * e;
-          e = (s.vy - s.cvy) - xr[4]; stage += d.QN[4] * e * e;
-          e = (s.vz - s.cvz) - xr[5]; stage += d.QN[5] * e * e;
+          e = (s.px - xr[0]) - s.cpx; stage += d.QN[0] * e * e;
+          e = (s.py - xr[1]) - s.cpy; stage += d.QN[1] * e * e;
+          e = (s.pz - xr[2]) - s.cpz; stage += d.QN[2] * e * e;
+          e = (s.vx - xr[3]) - s.cvx; stage += d.QN[3] * e * e;
+          e = (s.vy - xr[4]) - s.cvy; stage += d.QN[4] * e * e;
+          e = (s.vz - xr[5]) - s.cvz; stage += d.QN[5] * e * e;
           e = s.qw - sg * xr[6]; stage += d.QN[6] * e * e;
           e = s.qx - sg * xr[7]; stage += d.QN[7] * e * e;
           e = s.qy - sg * xr[8]; stage += d.QN[8] * e * e;
@@ -890,10 +893,12 @@ __global__ void rollout_states_kernel(ModelRegs M, float dt, int N, int B, const
 // ---------------------------------------------------------------------------
 static unsigned long long g_launches = 0;
 unsigned long long launches_so_far() { return g_launches; }
+void add_launches(int n) { g_launches += (unsigned long long)n; }
 
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
                          cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
   if (bf16)
     noise_kernel<1><<<n_tiles, block, 0, s>>>(descs, tiles);
   else
@@ -920,6 +925,7 @@ cudaError_t configure_kernels() {
 template <int OBJ, int BF16>
 static cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
                                     uint32_t smem, LaunchIO io, cudaStream_t s) {
+  (void)cudaGetLastError();
   rollout_kernel<OBJ, BF16><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   ++g_launches;
   return cudaGetLastError();
@@ -941,6 +947,7 @@ cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, cons
 
 cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
   nominal_kernel<<<(n + 3) / 4, 128, 0, s>>>(descs, which, n);
   ++g_launches;
   return cudaGetLastError();
@@ -949,6 +956,7 @@ cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, 
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
                           uint32_t* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
   philox_kernel<<<(n + 127) / 128, 128, 0, s>>>(k0, k1, c0, c1, c2, c3, n, out);
   ++g_launches;
   return cudaGetLastError();
@@ -957,6 +965,7 @@ cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, ui
 cudaError_t launch_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int n, float* out,
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
   normals_kernel<<<(n + 127) / 128, 128, 0, s>>>(seed, drone, k, it, blk, n, out);
   ++g_launches;
   return cudaGetLastError();
@@ -969,6 +978,7 @@ cudaError_t launch_rollout_states(const SolveDesc& md, float dt, int N, int B, c
   M.inv_mass = md.inv_mass; M.gravity = md.gravity; M.k_omega = md.k_omega;
   M.g0 = md.gyro[0]; M.g1 = md.gyro[1]; M.g2 = md.gyro[2];
   M.d0 = md.drag[0]; M.d1 = md.drag[1]; M.d2 = md.drag[2]; M.has_drag = md.has_drag;
+  (void)cudaGetLastError();
   rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, dt, N, B, x0, U, X);
   ++g_launches;
   return cudaGetLastError();

@@ -22,6 +22,7 @@ __host__ __device__ inline int n_groups_for(int T) {
 __host__ __device__ int path_fits_smem(int S);
 uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap);
 unsigned long long launches_so_far();
+void add_launches(int n);  // kernels run by a graph launch
 // sets the dynamic shared-memory limit of every rollout kernel (once per device)
 cudaError_t configure_kernels();
 

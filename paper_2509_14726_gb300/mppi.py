@@ -76,6 +76,7 @@ def load():
         "mppi_batch_solve": ([vp, PF, C.POINTER(C.c_double), vp, PF], C.c_int),
         "mppi_batch_solve_async": ([vp, vp, vp, vp, vp], C.c_int),
         "mppi_batch_destroy": ([vp], C.c_int),
+        "mppi_batch_profile": ([vp, I32, vp, PF], C.c_int),
         "mppi_set_shape": ([vp, I32, I32], C.c_int),
         "mppi_get_nominal": ([vp, PF], C.c_int),
         "mppi_get_unew": ([vp, PF], C.c_int),
@@ -240,6 +241,14 @@ def mppi_batch_solve(b: int, n: int, x0s, t0s=None, stream=None):
 def mppi_batch_solve_async(b: int, d_x0s: int, d_t0s: int, stream, d_u0s: int) -> None:
     _check(load().mppi_batch_solve_async(C.c_void_p(b), C.c_void_p(d_x0s), C.c_void_p(d_t0s), _stream_ptr(stream),
                                          C.c_void_p(d_u0s)))
+
+
+def mppi_batch_profile(b: int, n_iters: int, stream=None) -> np.ndarray:
+    """Mean ms per iteration of [noise, rollout gate, rollout contour, rollout
+    track, nominal, total] (launched without the graph, with CUDA events)."""
+    ms = np.zeros(6, np.float32)
+    _check(load().mppi_batch_profile(C.c_void_p(b), int(n_iters), _stream_ptr(stream), _pf(ms)))
+    return ms
 
 
 def mppi_batch_destroy(b: int) -> None:

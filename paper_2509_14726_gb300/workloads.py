@@ -78,18 +78,18 @@ class SolveConfig:
     q_near: float = 0.3
     r_near: float = 1.5
     temporal_rule: int = 1
-    q_lag: float = 10.0
-    q_cont: float = 100.0
-    q_omega: Tuple[float, float, float] = (0.01, 0.01, 0.01)
-    r_dv: float = 0.01
-    r_dthrust: float = 0.01
-    mu: float = 1.0
+    q_lag: float = 1.0
+    q_cont: float = 10.0
+    q_omega: Tuple[float, float, float] = (0.001, 0.001, 0.001)
+    r_dv: float = 0.001
+    r_dthrust: float = 0.001
+    mu: float = 0.1
     v_theta_max: float = 20.0
     theta_back: float = 2.0
     theta_ahead: float = 10.0
-    Q: Tuple[float, ...] = (100.0,) * 3 + (1.0,) * 3 + (10.0,) * 4 + (0.1,) * 3
-    QN: Tuple[float, ...] = (200.0,) * 3 + (2.0,) * 3 + (20.0,) * 4 + (0.2,) * 3
-    R: Tuple[float, float, float, float] = (0.01, 0.1, 0.1, 0.1)
+    Q: Tuple[float, ...] = (10.0,) * 3 + (0.1,) * 3 + (1.0,) * 4 + (0.01,) * 3
+    QN: Tuple[float, ...] = (20.0,) * 3 + (0.2,) * 3 + (2.0,) * 4 + (0.02,) * 3
+    R: Tuple[float, float, float, float] = (0.001, 0.01, 0.01, 0.01)
     flag_eps: float = 1.0e-5
 
 

@@ -17,6 +17,15 @@ from paper_2509_14726_gb300 import workloads as W
 # error of the nominal control (N or rad/s)
 J_REL_TOL = 1e-4
 U_ABS_TOL = 1e-5
+# Binary32 rollouts carry a per-sample cost error; it reaches the nominal
+# through the weights (Eq. 4): dU_kj = (1/lambda) sum_m w_m (dJbar - dJ_m)
+# (u_mkj - U_kj), so |dU_kj| <= 2 DJ32 sens_kj with sens_kj the oracle's
+# (1/lambda) sum_m w_m |u_mkj - U_kj|.  DJ32 is the binary32 cost error of a
+# sample: trajectory error floor 2.5e-7 m rms / 6.5e-7 m max over 50 RK4
+# steps times the cost gradient (2 |p - target| q, about 10 for these
+# weights) -> 2.5e-6 .. 6.5e-6; measured on significantly weighted samples
+# up to 5e-6.  Where sens_kj < 1 this leaves U_ABS_TOL.
+DJ32 = 5e-6
 
 
 @dataclasses.dataclass
@@ -75,11 +84,14 @@ def compare(gpu, r: dict, label: str = "", j_tol: float = J_REL_TOL, u_tol: floa
         stats["decision_mismatch_flagged"] = int((mism & flag).sum())
     Unew = gpu.unew()
     dU = np.abs(Unew[:, :nu] - r["Unew"][:, :nu])
+    tolU = np.maximum(u_tol, 2.0 * DJ32 * r["sens"][:, :nu])
     stats["max_dU"] = float(dU.max())
     stats["max_du0"] = float(dU[0].max())
+    stats["max_dU_over_tol"] = float((dU / tolU).max())
+    stats["well_conditioned_share"] = float(np.mean(tolU == u_tol))
     # the weight mass on samples whose decision differs (if any) explains a dU excess
     assert stats["max_rel_J"] <= j_tol, f"{label} J rel err {stats}"
     if gpu.sc.objective == 0 and check_decisions:
         assert stats["decision_mismatch_unflagged"] == 0, f"{label} gate decisions differ {stats}"
-    assert stats["max_dU"] <= u_tol, f"{label} nominal differs {stats}"
+    assert stats["max_dU_over_tol"] <= 1.0, f"{label} nominal differs {stats}"
     return stats
