@@ -244,6 +244,46 @@ int mppi_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_
 int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B,
                         const float* d_x0, const float* d_U, float* d_X, void* stream);
 
+/* A solve for callers that cannot allocate device memory while they run.
+ * The paper has no counterpart: this is an interface for integration.
+ *
+ * Some callers must not call cudaMalloc/cudaFree on their hot path: a control
+ * loop certified to allocate only at start-up, a process whose GPU memory is
+ * owned by another allocator, or a loop that cannot take the device-wide
+ * synchronisation an allocation may cause.  mppi_create allocates, so those
+ * callers use this call instead.  It runs the same noise and rollout kernels
+ * as mppi_solve but allocates nothing: every per-solve scratch buffer lives in
+ * one 16 MiB array in device memory that each GPU loading the library holds
+ * until the process exits.
+ *
+ * It is stateless: one solve from the caller's nominal d_U [N][5] (device,
+ * float32, unchanged), Philox iteration `iter` and gate index `gate`, as the
+ * first solve of a fresh controller would do it with that nominal (no
+ * previous x0, no pass counts of a previous nominal, no progress state).
+ * Outputs: d_Unew [N][5] (the weighted average, before any shift; warm
+ * starting is the caller's: shift it by one row for the next call) and d_u0
+ * [5], both device memory.  model and params are host structs read during the
+ * call; d_track holds DEVICE pointers to the gate / path / reference tables.
+ * d_x0 is device memory [13]; t0 selects the tracking window.
+ *
+ * Limit: the scratch must fit in 16 MiB (about 16 K N (16 + 4 for
+ * contouring) bytes of noise plus small tables: e.g. K = 8192 with N = 100,
+ * or K = 16384 with N = 50); larger sizes return MPPI_ERR_ARG with the needed
+ * byte count in mppi_last_error().
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and sets kernel
+ * attributes; make that first call before any stream capture.  Every call on
+ * a device shares the one array and leaves its contents behind; each call
+ * clears what must start at zero.  Calls whose work overlaps on the GPU (two
+ * streams, or two threads) race on the array and give wrong results: issue
+ * them on one stream, or order them.  Asynchronous: returns after enqueueing
+ * on `stream`.  Errors: MPPI_ERR_ARG (null pointer, bad sizes, scratch limit),
+ * MPPI_ERR_CUDA. */
+int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t* params, const mppi_track_t* d_track,
+                       const float* d_x0, double t0, const float* d_U, uint32_t iter, int32_t gate,
+                       void* stream, float* d_Unew, float* d_u0);
+
 /* Device memory the handle holds, bytes. */
 int mppi_device_bytes(mppi_handle h, size_t* bytes);
 /* Device memory a handle with these params would hold, bytes. */

@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libmppi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
-SOURCES = ["mppi_kernels.cu", "mppi_api.cu", "mppi_serve.cu"]
+SOURCES = ["mppi_kernels.cu", "mppi_api.cu", "mppi_serve.cu", "mppi_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -103,6 +103,8 @@ void hostio_free(HostIO& io) {
 
 }  // namespace
 
+void mppi::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct mppi_s {
   mppi_model_t model;
   mppi_params_t params;

@@ -98,6 +98,8 @@ def load():
         "mppi_estimate_bytes": ([C.POINTER(Params), C.POINTER(TrackC), C.POINTER(sz)], C.c_int),
         "mppi_kernel_launches": ([], C.c_uint64),
         "mppi_abi_sizes": ([C.POINTER(sz)], C.c_int),
+        "mppi_solve_noalloc": ([C.POINTER(Model), C.POINTER(Params), C.POINTER(TrackC), vp, C.c_double, vp, U32, I32,
+                                vp, vp, vp], C.c_int),
         "mppi_last_error": ([], C.c_char_p),
         "mppi_version": ([], C.c_char_p),
     }
@@ -347,6 +349,15 @@ def mppi_normals(seed, drone, k, it, blk, n: int, d_out: int, stream=None) -> No
 def mppi_rollout_states(model: Model, dt: float, N: int, B: int, d_x0: int, d_U: int, d_X: int, stream=None):
     _check(load().mppi_rollout_states(C.byref(model), float(dt), N, B, C.c_void_p(d_x0), C.c_void_p(d_U),
                                       C.c_void_p(d_X), _stream_ptr(stream)))
+
+
+def mppi_solve_noalloc(model: Model, params: Params, d_track: TrackC, d_x0: int, t0: float, d_U: int, it: int,
+                       gate: int, stream, d_Unew: int, d_u0: int) -> None:
+    """Stateless solve whose scratch is the library's static device array
+    (no device allocation); d_track holds device pointers."""
+    _check(load().mppi_solve_noalloc(C.byref(model), C.byref(params), C.byref(d_track), C.c_void_p(d_x0), float(t0),
+                                     C.c_void_p(d_U), int(it) & 0xFFFFFFFF, int(gate), _stream_ptr(stream),
+                                     C.c_void_p(d_Unew), C.c_void_p(d_u0)))
 
 
 def mppi_device_bytes(h: int) -> int:

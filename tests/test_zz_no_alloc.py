@@ -1,0 +1,94 @@
+"""The allocation-free solve gives the handle API's result.
+
+mppi_solve_noalloc exists for callers that may not allocate device memory
+while they run (a control loop that allocates only at start-up, a process
+whose GPU memory belongs to another allocator, a loop that cannot absorb the
+synchronisation an allocation may bring).  It keeps its scratch in the
+library's static device array.  This test runs two solves in a row through it
+and through a handle (mppi_create + mppi_solve_async) with the same inputs and
+checks that u0 and the weighted nominal agree within the parity tolerance.
+The file is named to be collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2509_14726_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+U_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    from paper_2509_14726_gb300 import mppi
+    return mppi
+
+
+def _device_track(M, tr):
+    gates = torch.tensor(np.float32(tr.gates), device="cuda").contiguous()
+    path = torch.tensor(np.float32(tr.path), device="cuda").contiguous()
+    ref = torch.tensor(np.float32(tr.ref), device="cuda").contiguous()
+    t = M.TrackC()
+    t.n_gates, t.closed = gates.shape[0], int(bool(tr.closed))
+    t.gates = C.cast(C.c_void_p(gates.data_ptr()), M.PF)
+    t.S, t.L, t.path = path.shape[0], float(tr.L), C.cast(C.c_void_p(path.data_ptr()), M.PF)
+    t.T, t.dt_ref, t.ref = ref.shape[0], float(tr.dt_ref), C.cast(C.c_void_p(ref.data_ptr()), M.PF)
+    return t, (gates, path, ref)
+
+
+def test_noalloc_matches_the_handle_path_twice(M):
+    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_GATE)
+    sc.temporal_rule = 0  # stateless call: no pass counts of a previous nominal
+    mc, sc, tr = W.f32_model(mc), W.f32_solve(sc), tr.as_f32()
+    ctl = M.Controller(mc, sc, tr)
+    d_track, keep = _device_track(M, tr)
+    stream = torch.cuda.Stream()
+    d_x0 = torch.tensor(np.float32(x0), device="cuda")
+    d_u0_h = torch.zeros(5, dtype=torch.float32, device="cuda")
+    d_u0_s = torch.zeros(5, dtype=torch.float32, device="cuda")
+    d_U = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
+    d_U[:, 0] = float(np.float32(mc.mass) * np.float32(mc.gravity))
+    d_Unew = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
+    free_before_second = None
+    for call in range(2):
+        with torch.cuda.stream(stream):
+            M.mppi_solve_async(ctl.h, d_x0.data_ptr(), 0.0, stream, d_u0_h.data_ptr())
+            if call == 1:
+                torch.cuda.synchronize()
+                free_before_second = torch.cuda.mem_get_info()[0]
+            M.mppi_solve_noalloc(ctl.model, ctl.params, d_track, d_x0.data_ptr(), 0.0, d_U.data_ptr(), call, 0,
+                                 stream, d_Unew.data_ptr(), d_u0_s.data_ptr())
+        stream.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before_second
+        u_h = d_u0_h.cpu().numpy()
+        u_s = d_u0_s.cpu().numpy()
+        U_h = ctl.unew()
+        U_s = d_Unew.cpu().numpy()
+        assert np.max(np.abs(u_s[:4] - u_h[:4])) <= U_TOL, (call, u_s, u_h)
+        assert np.max(np.abs(U_s[:, :4] - U_h[:, :4])) <= U_TOL, call
+        # warm start for the next call: shift by one row, repeat the last
+        d_U = torch.cat([d_Unew[1:], d_Unew[-1:]], dim=0).contiguous()
+    ctl.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(M):
+    mc, sc, tr, x0 = W.c4_precision()
+    p = M.make_params(sc)
+    d_track, keep = _device_track(M, tr)
+    dummy = torch.zeros(1024, dtype=torch.float32, device="cuda")
+    rc = M.load().mppi_solve_noalloc(C.byref(M.make_model(mc)), C.byref(p), C.byref(d_track),
+                                     C.c_void_p(dummy.data_ptr()), 0.0, C.c_void_p(dummy.data_ptr()), 0, 0, None,
+                                     C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()))
+    assert rc == M.MPPI_ERR_ARG
+    assert b"static maximum" in M.load().mppi_last_error()
