@@ -38,9 +38,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic FP32 operations per rollout step (FMA = 2, min/max/compare = 1,
-# rsqrt/sincos = 1), counted from the kernel source; see the design doc
-FLOPS_PER_STEP = {0: 485.0, 1: 520.0, 2: 500.0}
+# algorithmic FP32 operations per rollout step (FMA = 2, add/mul/min/max/
+# compare = 1, rsqrt = 1): sampling, RK4, objective, penalty and cost sum,
+# counted from the kernel's arithmetic; the derivation is in the design doc
+FLOPS_PER_STEP = {0: 423.0, 1: 491.0, 2: 478.0}
 
 
 def parse():

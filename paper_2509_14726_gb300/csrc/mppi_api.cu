@@ -137,7 +137,11 @@ struct mppi_batch_s {
     uint32_t smem;
     int n_tiles;
     Tile* d_tiles;
+    Tile* d_noise_tiles;  // the same tiles, for this group's own noise launch
   };
+  std::vector<cudaStream_t> branch_streams;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[8] = {};
   std::vector<Group> rollout_groups;
   struct NGroup {
     int bf16, block, n_tiles;
@@ -154,6 +158,13 @@ struct mppi_batch_s {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev = nullptr;
   int kernels_per_solve = 0;  // kernels one launch of the sequence runs
+  // second graph whose inputs/outputs are the plan's own device buffers
+  // (the device-resident async path copies into / out of them)
+  cudaGraph_t graph_dev = nullptr;
+  cudaGraphExec_t exec_dev = nullptr;
+  float* d_x0s = nullptr;
+  double* d_t0s = nullptr;
+  float* d_u0s = nullptr;
 };
 
 namespace {
@@ -173,7 +184,8 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
     return fail(MPPI_ERR_ARG, "unknown noise dtype");
   if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
   int blk = p->block ? p->block : 128;
-  if (blk < 32 || blk > kMaxBlock || blk % 32) return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, 512]", blk);
+  if (blk < 32 || blk > rollout_max_block() || blk % 32)
+    return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
   if (t->n_gates < 0 || t->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p->objective == MPPI_OBJ_GATE && (t->n_gates < 1 || !t->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs at least one gate");
@@ -772,6 +784,27 @@ int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t 
 // ---------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------
+static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s);
+
+// Captured form: every rollout group gets its own branch (its own noise
+// launch, then its rollout launch), so the groups' kernels overlap and fill
+// each other's tails; the branches join before the nominal rollout.
+static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
+  const int G = (int)b->rollout_groups.size();
+  if (G <= 1 || (int)b->branch_streams.size() < G) return batch_enqueue(b, io, s);
+  CU(cudaEventRecord(b->fork, s));
+  for (int i = 0; i < G; ++i) {
+    const auto& g = b->rollout_groups[i];
+    cudaStream_t bs = b->branch_streams[i];
+    CU(cudaStreamWaitEvent(bs, b->fork, 0));
+    CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs));
+    CU(cudaEventRecord(b->join[i], bs));
+    CU(cudaStreamWaitEvent(s, b->join[i], 0));
+  }
+  return MPPI_OK;
+}
+
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s));
   for (const auto& g : b->rollout_groups)
@@ -783,7 +816,13 @@ int mppi_batch_destroy(mppi_batch b) {
   if (!b) return MPPI_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->exec_dev) cudaGraphExecDestroy(b->exec_dev);
+  if (b->graph_dev) cudaGraphDestroy(b->graph_dev);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaStream_t bs : b->branch_streams) cudaStreamDestroy(bs);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
   if (b->ev) cudaEventDestroy(b->ev);
   hostio_free(b->io);
   if (b->dev) cudaFree(b->dev);
@@ -844,7 +883,9 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   size_t tiles_total = 0;
   for (auto& g : rg) tiles_total += g.second.size();
   for (auto& g : ng) tiles_total += g.second.size();
-  const size_t bytes = al256(sizeof(SolveDesc) * n) + al256(sizeof(Tile) * tiles_total) + al256(sizeof(int32_t) * (which.size() + 1));
+  const size_t bytes = al256(sizeof(SolveDesc) * n) + al256(sizeof(Tile) * tiles_total) +
+                       al256(sizeof(int32_t) * (which.size() + 1)) + al256(sizeof(float) * 13 * n) +
+                       al256(sizeof(double) * n) + al256(sizeof(float) * 5 * n);
   if (cudaMalloc(&b->dev, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -866,7 +907,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     auto& v = rg[gi].second;
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
-    b->rollout_groups.push_back({rg[gi].first.obj, rg[gi].first.bf16, rg[gi].first.block, rsmem[gi], (int)v.size(), tp});
+    b->rollout_groups.push_back({rg[gi].first.obj, rg[gi].first.bf16, rg[gi].first.block, rsmem[gi], (int)v.size(), tp, tp});
     tp += v.size();
   }
   for (auto& g : ng) {
@@ -878,10 +919,18 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   }
   c += al256(sizeof(Tile) * tiles_total);
   b->d_which = reinterpret_cast<int32_t*>(c);
+  c += al256(sizeof(int32_t) * (which.size() + 1));
+  b->d_x0s = reinterpret_cast<float*>(c);
+  c += al256(sizeof(float) * 13 * n);
+  b->d_t0s = reinterpret_cast<double*>(c);
+  c += al256(sizeof(double) * n);
+  b->d_u0s = reinterpret_cast<float*>(c);
   b->n_which = (int)which.size();
   if (!which.empty() && cudaMemcpy(b->d_which, which.data(), sizeof(int32_t) * which.size(), cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "work list upload failed"));
   b->kernels_per_solve = (int)b->noise_groups.size() + (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
+  if (b->use_graph && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8)
+    b->kernels_per_solve = 2 * (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
   int rc = hostio_alloc(b->io, n);
   if (rc) return cleanup(rc);
   if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
@@ -889,6 +938,19 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   if (b->use_graph) {
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "stream creation failed"));
+    const int G = (int)b->rollout_groups.size();
+    if (G > 1 && G <= 8) {
+      if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
+      for (int i = 0; i < G; ++i) {
+        cudaStream_t bs;
+        if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess)
+          return cleanup(fail(MPPI_ERR_CUDA, "stream creation failed"));
+        b->branch_streams.push_back(bs);
+        if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+          return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
+      }
+    }
     LaunchIO io;
     memset(&io, 0, sizeof io);
     io.x0 = b->io.d_x0;
@@ -897,7 +959,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     io.status = b->io.d_status;
     if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
-    int rc2 = batch_enqueue(b, io, b->cap_stream);
+    int rc2 = batch_enqueue_branches(b, io, b->cap_stream);
     cudaError_t e1 = cudaEventRecordWithFlags(b->ev, b->cap_stream, cudaEventRecordExternal);
     cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
     cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
@@ -905,6 +967,20 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
       return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed (%s / %s / %s)", cudaGetErrorString(e1),
                           cudaGetErrorString(e2), cudaGetErrorString(e3)));
     if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+      return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
+    LaunchIO iod;
+    memset(&iod, 0, sizeof iod);
+    iod.x0 = b->d_x0s;
+    iod.t0 = b->d_t0s;
+    iod.u0 = b->d_u0s;
+    iod.status = nullptr;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
+    int rc3 = batch_enqueue_branches(b, iod, b->cap_stream);
+    cudaError_t f2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
+    cudaError_t f3 = cudaStreamEndCapture(b->cap_stream, &b->graph_dev);
+    if (rc3 || f2 || f3) return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed"));
+    if (cudaGraphInstantiate(&b->exec_dev, b->graph_dev, 0) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
   }
   *out = b;
@@ -1008,6 +1084,14 @@ int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s
   io.u0 = d_u0s;
   io.status = nullptr;
   if (!d_t0s) return fail(MPPI_ERR_ARG, "d_t0s is required");
+  if (b->use_graph && b->exec_dev) {
+    CU(cudaMemcpyAsync(b->d_x0s, d_x0s, sizeof(float) * 13 * b->n, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(b->d_t0s, d_t0s, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, s));
+    CU(cudaGraphLaunch(b->exec_dev, s));
+    add_launches(b->kernels_per_solve);
+    CU(cudaMemcpyAsync(d_u0s, b->d_u0s, sizeof(float) * 5 * b->n, cudaMemcpyDeviceToDevice, s));
+    return MPPI_OK;
+  }
   rc = batch_enqueue(b, io, s);
   if (rc) return rc;
   CU(launch_nominal(b->d_descs, b->d_which, b->n_which, s));

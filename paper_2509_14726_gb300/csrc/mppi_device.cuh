@@ -188,89 +188,109 @@ struct ModelRegs {
   int has_drag;
 };
 
-__device__ __forceinline__ void accel(const ModelRegs& M, float ac, float qw, float qx, float qy, float qz,
-                                      float vx, float vy, float vz, float& ax, float& ay, float& az) {
-  // thrust along the body z axis: R(q) e_z
-  const float bx = 2.0f * (qx * qz + qw * qy);
-  const float by = 2.0f * (qy * qz - qw * qx);
-  const float bz = 1.0f - 2.0f * (qx * qx + qy * qy);
-  ax = ac * bx;
-  ay = ac * by;
-  az = ac * bz - M.gravity;
-  if (M.has_drag) {
-    // - R D R^T v
-    const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = bx;
-    const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = by;
-    const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = bz;
-    const float bv0 = M.d0 * (r00 * vx + r10 * vy + r20 * vz);
-    const float bv1 = M.d1 * (r01 * vx + r11 * vy + r21 * vz);
-    const float bv2 = M.d2 * (r02 * vx + r12 * vy + r22 * vz);
-    ax -= r00 * bv0 + r01 * bv1 + r02 * bv2;
-    ay -= r10 * bv0 + r11 * bv1 + r12 * bv2;
-    az -= r20 * bv0 + r21 * bv1 + r22 * bv2;
-  }
+// Body-z thrust acceleration R(q) e_z c/m - g e_z, with the factor 2 of R
+// folded into ac2 = 2 c/m and acg = c/m - g (both per step).
+__device__ __forceinline__ void accel_nodrag(float ac2, float acg, float qw, float qx, float qy, float qz, float& ax,
+                                             float& ay, float& az) {
+  ax = ac2 * (qx * qz + qw * qy);
+  ay = ac2 * (qy * qz - qw * qx);
+  az = acg - ac2 * (qx * qx + qy * qy);
 }
 
-__device__ __forceinline__ void attitude_rate(const ModelRegs& M, float kcx, float kcy, float kcz, float qw,
-                                              float qx, float qy, float qz, float wx, float wy, float wz,
-                                              float& dqw, float& dqx, float& dqy, float& dqz, float& dwx,
-                                              float& dwy, float& dwz) {
-  const float hx = 0.5f * wx, hy = 0.5f * wy, hz = 0.5f * wz;
-  dqw = -(qx * hx + qy * hy + qz * hz);
-  dqx = qw * hx + qy * hz - qz * hy;
-  dqy = qw * hy + qz * hx - qx * hz;
-  dqz = qw * hz + qx * hy - qy * hx;
-  // tau = J k_w (w_cmd - w):  w_dot = k_w (w_cmd - w) - J^-1 (w x J w)
+// the same plus the body-frame drag - R D R^T v
+__device__ __forceinline__ void accel_drag(const ModelRegs& M, float ac2, float acg, float qw, float qx, float qy,
+                                           float qz, float vx, float vy, float vz, float& ax, float& ay, float& az) {
+  accel_nodrag(ac2, acg, qw, qx, qy, qz, ax, ay, az);
+  const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
+  const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
+  const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
+  const float bv0 = M.d0 * (r00 * vx + r10 * vy + r20 * vz);
+  const float bv1 = M.d1 * (r01 * vx + r11 * vy + r21 * vz);
+  const float bv2 = M.d2 * (r02 * vx + r12 * vy + r22 * vz);
+  ax -= r00 * bv0 + r01 * bv1 + r02 * bv2;
+  ay -= r10 * bv0 + r11 * bv1 + r12 * bv2;
+  az -= r20 * bv0 + r21 * bv1 + r22 * bv2;
+}
+
+// Twice the quaternion rate, q * (0, w) (the 1/2 of Eq. 2 is folded into the
+// step sizes), and the body-rate derivative k_w (w_cmd - w) - J^-1 (w x J w)
+// with kc = k_w w_cmd precomputed per step.
+__device__ __forceinline__ void attitude_rate2(const ModelRegs& M, float kcx, float kcy, float kcz, float qw,
+                                               float qx, float qy, float qz, float wx, float wy, float wz, float& dqw,
+                                               float& dqx, float& dqy, float& dqz, float& dwx, float& dwy,
+                                               float& dwz) {
+  dqw = -(qx * wx + qy * wy + qz * wz);
+  dqx = qw * wx + qy * wz - qz * wy;
+  dqy = qw * wy + qz * wx - qx * wz;
+  dqz = qw * wz + qx * wy - qy * wx;
   dwx = kcx - M.k_omega * wx - M.g0 * wy * wz;
   dwy = kcy - M.k_omega * wy - M.g1 * wz * wx;
   dwz = kcz - M.k_omega * wz - M.g2 * wx * wy;
 }
 
-// One RK4 step with the input (c, w_cmd) held.  Writes the position increment
-// (the exact RK4 increment, before compensated accumulation) to dp.
+// One classical RK4 step (Eq. 2 with the CTBR input held over the step).
+// Writes the position increment (exact RK4 increment, before the compensated
+// accumulation) to dp.  Without drag the accelerations depend on q only, so
+// the stage velocities are not formed:  p += h v + h^2/6 (a1 + a2 + a3),
+// v += h/6 (a1 + 2 a2 + 2 a3 + a4).
+template <bool DRAG>
 __device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, float cx, float cy, float cz,
                                          float h, float& dpx, float& dpy, float& dpz) {
   const float ac = c * M.inv_mass;
+  const float ac2 = 2.f * ac, acg = ac - M.gravity;
   const float kcx = M.k_omega * cx, kcy = M.k_omega * cy, kcz = M.k_omega * cz;
-  const float h2 = 0.5f * h;
+  const float h2 = 0.5f * h, h4 = 0.25f * h;
   float dqw, dqx, dqy, dqz, dwx, dwy, dwz, ax, ay, az;
   // stage 1
-  attitude_rate(M, kcx, kcy, kcz, s.qw, s.qx, s.qy, s.qz, s.wx, s.wy, s.wz, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
-  accel(M, ac, s.qw, s.qx, s.qy, s.qz, s.vx, s.vy, s.vz, ax, ay, az);
+  attitude_rate2(M, kcx, kcy, kcz, s.qw, s.qx, s.qy, s.qz, s.wx, s.wy, s.wz, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, s.qw, s.qx, s.qy, s.qz, s.vx, s.vy, s.vz, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, s.qw, s.qx, s.qy, s.qz, ax, ay, az);
   float sqw = dqw, sqx = dqx, sqy = dqy, sqz = dqz, swx = dwx, swy = dwy, swz = dwz;
-  float sax = ax, say = ay, saz = az;  // acc1 + 2 acc2 + 2 acc3 + acc4
-  float pax = ax, pay = ay, paz = az;  // acc1 + acc2 + acc3 (position increment)
+  float sax = ax, say = ay, saz = az;  // a1 + 2 a2 + 2 a3 + a4
+  float pax = ax, pay = ay, paz = az;  // a1 + a2 + a3
+  float vx2 = 0.f, vy2 = 0.f, vz2 = 0.f;
   // stage 2
-  float qw2 = s.qw + h2 * dqw, qx2 = s.qx + h2 * dqx, qy2 = s.qy + h2 * dqy, qz2 = s.qz + h2 * dqz;
+  float qw2 = s.qw + h4 * dqw, qx2 = s.qx + h4 * dqx, qy2 = s.qy + h4 * dqy, qz2 = s.qz + h4 * dqz;
   float wx2 = s.wx + h2 * dwx, wy2 = s.wy + h2 * dwy, wz2 = s.wz + h2 * dwz;
-  float vx2 = s.vx + h2 * ax, vy2 = s.vy + h2 * ay, vz2 = s.vz + h2 * az;
-  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
-  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  if (DRAG) { vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az; }
+  attitude_rate2(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
   sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
   swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
   sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
   pax += ax; pay += ay; paz += az;
   // stage 3
-  qw2 = s.qw + h2 * dqw; qx2 = s.qx + h2 * dqx; qy2 = s.qy + h2 * dqy; qz2 = s.qz + h2 * dqz;
+  qw2 = s.qw + h4 * dqw; qx2 = s.qx + h4 * dqx; qy2 = s.qy + h4 * dqy; qz2 = s.qz + h4 * dqz;
   wx2 = s.wx + h2 * dwx; wy2 = s.wy + h2 * dwy; wz2 = s.wz + h2 * dwz;
-  vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az;
-  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
-  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  if (DRAG) { vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az; }
+  attitude_rate2(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
   sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
   swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
   sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
   pax += ax; pay += ay; paz += az;
   // stage 4
-  qw2 = s.qw + h * dqw; qx2 = s.qx + h * dqx; qy2 = s.qy + h * dqy; qz2 = s.qz + h * dqz;
+  qw2 = s.qw + h2 * dqw; qx2 = s.qx + h2 * dqx; qy2 = s.qy + h2 * dqy; qz2 = s.qz + h2 * dqz;
   wx2 = s.wx + h * dwx; wy2 = s.wy + h * dwy; wz2 = s.wz + h * dwz;
-  vx2 = s.vx + h * ax; vy2 = s.vy + h * ay; vz2 = s.vz + h * az;
-  attitude_rate(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
-  accel(M, ac, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  if (DRAG) { vx2 = s.vx + h * ax; vy2 = s.vy + h * ay; vz2 = s.vz + h * az; }
+  attitude_rate2(M, kcx, kcy, kcz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
   sqw += dqw; sqx += dqx; sqy += dqy; sqz += dqz;
   swx += dwx; swy += dwy; swz += dwz;
   sax += ax; say += ay; saz += az;
-  // combine: p += h v + h^2/6 (a1 + a2 + a3), v += h/6 (a1 + 2 a2 + 2 a3 + a4)
-  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+  // combine
+  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6, h12 = 0.5f * h6;
   dpx = h * s.vx + hh6 * pax;
   dpy = h * s.vy + hh6 * pay;
   dpz = h * s.vz + hh6 * paz;
@@ -280,7 +300,7 @@ __device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, f
   kahan_add(s.vx, s.cvx, h6 * sax);
   kahan_add(s.vy, s.cvy, h6 * say);
   kahan_add(s.vz, s.cvz, h6 * saz);
-  float qw1 = s.qw + h6 * sqw, qx1 = s.qx + h6 * sqx, qy1 = s.qy + h6 * sqy, qz1 = s.qz + h6 * sqz;
+  const float qw1 = s.qw + h12 * sqw, qx1 = s.qx + h12 * sqx, qy1 = s.qy + h12 * sqy, qz1 = s.qz + h12 * sqz;
   s.wx += h6 * swx;
   s.wy += h6 * swy;
   s.wz += h6 * swz;

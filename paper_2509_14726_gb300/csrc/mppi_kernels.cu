@@ -184,11 +184,13 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
       d.Z4[idx] = z;
     }
     if (five) {
-      const float4 z5 = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 1u);
+      // the 5th normal is the first output of block 1 (one Box-Muller pair)
+      const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
+      const float z5 = box_muller(x5.x, x5.y).x;
       if (BF16)
-        d.Z5b[idx] = __float2bfloat16_rn(z5.x);
+        d.Z5b[idx] = __float2bfloat16_rn(z5);
       else
-        d.Z5[idx] = z5.x;
+        d.Z5[idx] = z5;
     }
   }
 }
@@ -273,8 +275,22 @@ __device__ __forceinline__ double part_value(double raw, int f64) {
 // ---------------------------------------------------------------------------
 // K2: rollout + cost + per-block weights + merge (last block)
 // ---------------------------------------------------------------------------
+// Occupancy of the rollout kernel is register-bound; MPPI_ROLLOUT_MIN_BLOCKS
+// (build option) caps the registers so that this many 128-thread blocks fit
+// on an SM (blocks are then limited to 128 threads).
+#ifndef MPPI_ROLLOUT_MIN_BLOCKS
+#define MPPI_ROLLOUT_MIN_BLOCKS 0
+#endif
+#if MPPI_ROLLOUT_MIN_BLOCKS > 0
+#define MPPI_ROLLOUT_BOUNDS __launch_bounds__(128, MPPI_ROLLOUT_MIN_BLOCKS)
+#else
+#define MPPI_ROLLOUT_BOUNDS __launch_bounds__(kMaxBlock)
+#endif
+
+int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
+
 template <int OBJ, int BF16>
-__global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __restrict__ descs,
+__global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__ descs,
                                                             const Tile* __restrict__ tiles, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) SolveDesc sd;
@@ -457,14 +473,19 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
     s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
     const float h = d.dt;
     // objective state
-    int gi = 0;
-    GateF g, g0;
-    float sa = 0.f;
+    // gate progress state: target gate, p_k - g for it (ra), its plane distance
+    int gi = 0, gate_start = 0, slot0 = 0;
+    GateF g;
+    float sa = 0.f, rax = 0.f, ray = 0.f, raz = 0.f;
+    const float q_near = d.q_near, r_near2 = d.r_near2;
     if (OBJ == MPPI_OBJ_GATE) {
-      gi = st->gate + s_adv;
-      g = sG[gate_slot(gi, d.n_gates, d.closed)];
-      g0 = g;
-      sa = plane_dist(g, s.px, s.py);
+      gi = gate_start = st->gate + s_adv;
+      slot0 = gate_slot(gi, d.n_gates, d.closed);
+      g = sG[slot0];
+      rax = s.px - g.cx;
+      ray = s.py - g.cy;
+      raz = s.pz - g.cz;
+      sa = g.nx * rax + g.ny * ray;
     }
     int node = 0;
     float frac_m = 0.f, frac_c = 0.f, vth = 0.f, c_prev = 0.f;
@@ -474,14 +495,23 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
       vth = s_vth0;
       c_prev = st->has_prev ? st->c_last : d.hover;
     }
-    float z[kNU];
+    // loop invariants in registers (the descriptor lives in shared memory)
+    const float sg0 = d.sigma[0], sg1 = d.sigma[1], sg2 = d.sigma[2], sg3 = d.sigma[3];
+    const float lo0 = d.u_min[0], lo1 = d.u_min[1], lo2 = d.u_min[2], lo3 = d.u_min[3];
+    const float hi0 = d.u_max[0], hi1 = d.u_max[1], hi2 = d.u_max[2], hi3 = d.u_max[3];
+    const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
+    // software pipeline: the next step's noise is in flight during this step
+    float z[kNU], zn[kNU];
+    load_noise<BF16>(d, (size_t)m, zn, five);
     for (int k = 0; k < N; ++k) {
-      load_noise<BF16>(d, (size_t)k * K + m, z, five);
+#pragma unroll
+      for (int j = 0; j < kNU; ++j) z[j] = zn[j];
+      if (k + 1 < N) load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
       const float* Uk = sU + kNU * k;
-      const float u0 = clampf(Uk[0] + d.sigma[0] * z[0], d.u_min[0], d.u_max[0]);
-      const float u1 = clampf(Uk[1] + d.sigma[1] * z[1], d.u_min[1], d.u_max[1]);
-      const float u2 = clampf(Uk[2] + d.sigma[2] * z[2], d.u_min[2], d.u_max[2]);
-      const float u3 = clampf(Uk[3] + d.sigma[3] * z[3], d.u_min[3], d.u_max[3]);
+      const float u0 = clampf(Uk[0] + sg0 * z[0], lo0, hi0);
+      const float u1 = clampf(Uk[1] + sg1 * z[1], lo1, hi1);
+      const float u2 = clampf(Uk[2] + sg2 * z[2], lo2, hi2);
+      const float u3 = clampf(Uk[3] + sg3 * z[3], lo3, hi3);
       float stage = 0.f;
       if (OBJ == MPPI_OBJ_TRACK) {
         // Eq. 8 stage term on x_k and u_k
@@ -505,36 +535,52 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
         const float du = u0 - d.hover;
         stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
       }
-      // positions at the start of the step (value and compensation kept apart)
-      const float apx = s.px, apy = s.py, apz = s.pz, acx = s.cpx, acy = s.cpy, acz = s.cpz;
-      const float ax = apx - acx, ay = apy - acy, az = apz - acz;
-      float dpx, dpy, dpz;
-      rk4_step(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
-      const float bx = pxt(s), by = pyt(s), bz = pzt(s);
+      float near = 0.f;
       if (OBJ == MPPI_OBJ_GATE) {
-        // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g)
-        const float prog = dpx * ((apx - g.cx) - acx + ((s.px - g.cx) - s.cpx)) +
-                           dpy * ((apy - g.cy) - acy + ((s.py - g.cy) - s.cpy)) +
-                           dpz * ((apz - g.cz) - acz + ((s.pz - g.cz) - s.cpz));
-        const float ex = (apx - g0.cx) - acx, ey = (apy - g0.cy) - acy, ez = (apz - g0.cz) - acz;
+        // Eq. 7 near-gate term on p_k and the solve's current gate g0
+        float ex = rax, ey = ray, ez = raz;
+        if (gi != gate_start) {
+          const GateF& G0 = sG[slot0];
+          ex = (s.px - G0.cx) - s.cpx;
+          ey = (s.py - G0.cy) - s.cpy;
+          ez = (s.pz - G0.cz) - s.cpz;
+        }
         const float d0 = ex * ex + ey * ey + ez * ez;
-        stage = prog + (d0 < d.r_near2 ? d.q_near * d0 : 0.f);
-        const float sb = plane_dist(g, bx, by);
+        near = d0 < r_near2 ? q_near * d0 : 0.f;
+      }
+      float dpx, dpy, dpz;
+      if (M.has_drag)
+        rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+      else
+        rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+      if (OBJ == MPPI_OBJ_GATE) {
+        // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
+        // with both positions taken relative to g before rounding
+        float rbx = (s.px - g.cx) - s.cpx, rby = (s.py - g.cy) - s.cpy, rbz = (s.pz - g.cz) - s.cpz;
+        stage = dpx * (rax + rbx) + dpy * (ray + rby) + dpz * (raz + rbz) + near;
+        float sb = g.nx * rbx + g.ny * rby;
         if (sa < 0.f && sb >= 0.f) {
           const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
           const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
-          if (!open_track_done && ok_time && through_opening(g, sa, sb, ax, ay, az, bx - ax, by - ay, bz - az)) {
+          // crossing point on the segment, relative to the gate centre
+          const float a = sa / (sa - sb);
+          const float ex = rax + a * (rbx - rax), ey = ray + a * (rby - ray), ez = raz + a * (rbz - raz);
+          const bool open = fabsf(-g.ny * ex + g.nx * ey) <= g.hw && fabsf(ez) <= g.hh;
+          if (!open_track_done && ok_time && open) {
             ++passed;
             ++gi;
             if (first < 0) first = k;
             g = sG[gate_slot(gi, d.n_gates, d.closed)];
-            sa = plane_dist(g, bx, by);
-          } else {
-            sa = sb;
+            rbx = (s.px - g.cx) - s.cpx;
+            rby = (s.py - g.cy) - s.cpy;
+            rbz = (s.pz - g.cz) - s.cpz;
+            sb = g.nx * rbx + g.ny * rby;
           }
-        } else {
-          sa = sb;
         }
+        rax = rbx;
+        ray = rby;
+        raz = rbz;
+        sa = sb;
       } else if (OBJ == MPPI_OBJ_CONTOUR) {
         // Eq. 9 with the progress state (theta, v_theta), terms on x_{k+1}
         const float a = clampf(Uk[4] + d.sigma[4] * z[4], d.u_min[4], d.u_max[4]);
@@ -586,7 +632,7 @@ __global__ void __launch_bounds__(kMaxBlock) rollout_kernel(const SolveDesc* __r
           e = s.wz - xr[12]; stage += d.QN[12] * e * e;
         }
       }
-      stage += limit_penalty(d.w_limit, d.omega_max, d.z_floor, s);
+      stage += limit_penalty(w_limit, omega_max, z_floor, s);
       kahan_add(Jh, Jc, stage);
     }
   }
@@ -815,7 +861,10 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
       const float* u = d.unew + kNU * k;
       const float ax = pxt(s), ay = pyt(s), az = pzt(s);
       float dpx, dpy, dpz;
-      rk4_step(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+      if (M.has_drag)
+        rk4_step<true>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+      else
+        rk4_step<false>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
       const float bx = pxt(s), by = pyt(s), bz = pzt(s);
       const float sb = plane_dist(g, bx, by);
       if (sa < 0.f && sb >= 0.f) {
@@ -879,7 +928,10 @@ __global__ void rollout_states_kernel(ModelRegs M, float dt, int N, int B, const
   for (int k = 0; k < N; ++k) {
     const float* u = U + ((size_t)b * N + k) * 4;
     float dpx, dpy, dpz;
-    rk4_step(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+    if (M.has_drag)
+      rk4_step<true>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+    else
+      rk4_step<false>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
     float* r = o + (size_t)(k + 1) * kNX;
     r[0] = pxt(s); r[1] = pyt(s); r[2] = pzt(s);
     r[3] = s.vx - s.cvx; r[4] = s.vy - s.cvy; r[5] = s.vz - s.cvz;

@@ -27,6 +27,8 @@ void add_launches(int n);  // kernels run by a graph launch
 void set_last_error(const char* msg);
 // sets the dynamic shared-memory limit of every rollout kernel (once per device)
 cudaError_t configure_kernels();
+// largest block the rollout kernel was compiled for
+int rollout_max_block();
 
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
                          cudaStream_t s);

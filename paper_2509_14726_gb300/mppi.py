@@ -16,7 +16,7 @@ import numpy as np
 from . import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libmppi.so")
+LIB_PATH = os.environ.get("MPPI_LIB") or os.path.join(HERE, "lib", "libmppi.so")
 
 MPPI_OK, MPPI_ERR_ARG, MPPI_ERR_OOM, MPPI_ERR_CUDA, MPPI_ERR_TIMEOUT, MPPI_ERR_NOT_ADMITTED, MPPI_WARN_DEGENERATE = range(7)
 NOISE_F32, NOISE_BF16 = 0, 1
