@@ -168,7 +168,9 @@ int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const d
                      void* stream, float* u0s_out);
 
 /* Explicit batch plans (what mppi_solve_batch caches internally).
- * use_graph = 1 captures the launch sequence in a CUDA graph. */
+ * use_graph = 1 captures the launch sequence in a CUDA graph with one
+ * concurrent branch per (objective, noise type, block) group; use_graph = 2
+ * captures it as one serial chain; 0 launches without a graph. */
 int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_batch* out);
 int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* stream, float* u0s_out);
 /* device-side form: d_x0s [n][13], d_t0s [n], d_u0s [n][5]; asynchronous */

@@ -153,6 +153,7 @@ struct mppi_batch_s {
   void* dev = nullptr;
   HostIO io;
   bool use_graph = false;
+  bool branches = false;  // graph with one branch per rollout group
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -843,6 +844,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->hs.assign(hs, hs + n);
   for (int i = 0; i < n; ++i) b->versions.push_back(hs[i]->version);
   b->use_graph = use_graph != 0;
+  b->branches = use_graph == 1;
   // group tiles by launch configuration; longest horizons first (LPT)
   struct Key {
     int obj, bf16, block;
@@ -855,8 +857,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   std::vector<uint32_t> rsmem;
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
+  // longest tiles first: a tile's time grows with N (it holds <= block samples)
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-    return (long long)hs[a]->hd.N * hs[a]->hd.K > (long long)hs[c]->hd.N * hs[c]->hd.K;
+    if (hs[a]->hd.N != hs[c]->hd.N) return hs[a]->hd.N > hs[c]->hd.N;
+    return hs[a]->hd.K > hs[c]->hd.K;
   });
   std::vector<int32_t> which;
   for (int oi = 0; oi < n; ++oi) {
@@ -929,7 +933,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   if (!which.empty() && cudaMemcpy(b->d_which, which.data(), sizeof(int32_t) * which.size(), cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "work list upload failed"));
   b->kernels_per_solve = (int)b->noise_groups.size() + (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
-  if (b->use_graph && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8)
+  if (b->use_graph && b->branches && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8)
     b->kernels_per_solve = 2 * (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
   int rc = hostio_alloc(b->io, n);
   if (rc) return cleanup(rc);
@@ -939,7 +943,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "stream creation failed"));
     const int G = (int)b->rollout_groups.size();
-    if (G > 1 && G <= 8) {
+    if (b->branches && G > 1 && G <= 8) {
       if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
       for (int i = 0; i < G; ++i) {

@@ -22,6 +22,16 @@
 
 namespace mppi {
 
+// loop unrolling of the per-step loops (build options)
+#ifndef MPPI_NOISE_UNROLL
+#define MPPI_NOISE_UNROLL 1
+#endif
+#ifndef MPPI_ROLLOUT_UNROLL
+#define MPPI_ROLLOUT_UNROLL 1
+#endif
+constexpr int kNoiseUnroll = MPPI_NOISE_UNROLL;
+constexpr int kRolloutUnroll = MPPI_ROLLOUT_UNROLL;
+
 // bounded wait on an mbarrier phase; returns false after ~timeout_ns
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
@@ -171,6 +181,7 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
   if (d.ext_noise || m >= K || threadIdx.x >= d.block) return;
   const uint32_t iter = d.st->iter;
   const bool five = d.nu == 5;
+#pragma unroll kNoiseUnroll
   for (int k = 0; k < N; ++k) {
     const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
     const size_t idx = (size_t)k * K + m;
@@ -503,6 +514,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     // software pipeline: the next step's noise is in flight during this step
     float z[kNU], zn[kNU];
     load_noise<BF16>(d, (size_t)m, zn, five);
+#pragma unroll kRolloutUnroll
     for (int k = 0; k < N; ++k) {
 #pragma unroll
       for (int j = 0; j < kNU; ++j) z[j] = zn[j];

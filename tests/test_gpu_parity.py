@@ -131,7 +131,7 @@ def test_c1_first_solve(O, M):
     gpu.close()
 
 
-@pytest.mark.parametrize("K,N,block", [(1, 1, 32), (33, 3, 32), (1000, 13, 128), (3000, 20, 64), (5000, 7, 256)])
+@pytest.mark.parametrize("K,N,block", [(1, 1, 32), (33, 3, 32), (1000, 13, 128), (3000, 20, 64), (5000, 7, 128), (20000, 5, 64)])
 def test_ragged_tiles_and_merge_levels(O, M, K, N, block):
     """K not a multiple of the block, one tile, several tiles, and enough
     tiles for the two-level merge (more than 16)."""
