@@ -286,6 +286,66 @@ int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t* params, c
                        const float* d_x0, double t0, const float* d_U, uint32_t iter, int32_t gate,
                        void* stream, float* d_Unew, float* d_u0);
 
+/* ---------------- serving: continuous batching of many drones ------------ */
+/* A server owns many drones' resident controller state (nominal, Philox
+ * iteration, gate index, pass counts, progress state: a few KB each) and one
+ * device pool of scratch memory of a fixed budget.  Solve requests from the
+ * drones (each with its own K and N, up to the drone's caps) queue on the
+ * host; mppi_server_step admits queued requests in arrival order while their
+ * scratch (noise, costs, tile partials: about 16 K N bytes each, 20 K N for
+ * contouring) fits in the pool's free space, and launches them as one batch
+ * (the kernels of mppi_solve_batch) on the next free stream slot, so batches
+ * overlap on the device while later requests keep arriving.  A drone has at
+ * most one request in flight; its next request waits for the previous one.
+ * mppi_server_poll returns finished requests.  Each result equals what
+ * mppi_solve on a handle with the same state would give (same kernels, same
+ * per-solve reduction order).  The paper has no serving layer; this is the
+ * batching the GPU needs to run many controllers at their own rates. */
+typedef struct mppi_server_s* mppi_server;
+
+typedef struct {
+  int64_t request;   /* id returned by mppi_server_submit */
+  int32_t drone;
+  int32_t status;    /* mppi_status of the solve */
+  int32_t K, N;
+  float u0[5];
+  double t_submit;   /* mppi_clock() when submitted */
+  double t_launch;   /* when its batch was launched */
+  double t_done;     /* when a poll saw it finished */
+} mppi_result_t;
+
+/* Host monotonic clock in seconds (the server's timestamps). */
+double mppi_clock(void);
+
+/* max_drones: drones the server may hold; scratch_budget_bytes: device pool
+ * for in-flight requests; n_slots: batches that may be in flight at once
+ * (one stream each); max_batch: requests per batch.  Errors: MPPI_ERR_ARG,
+ * MPPI_ERR_OOM (the pool or the staging buffers), MPPI_ERR_CUDA. */
+int mppi_server_create(int32_t max_drones, size_t scratch_budget_bytes, int32_t n_slots, int32_t max_batch,
+                       mppi_server* out);
+/* Adds a drone (model, params with K_cap / N_cap = its largest request, and
+ * track, as for mppi_create; block must be 128 or less).  Writes its id. */
+int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_params_t* params,
+                          const mppi_track_t* track, int32_t* drone_out);
+/* Queues n requests (host arrays: drones [n], x0s [n][13], t0s [n], Ks [n],
+ * Ns [n]); writes their ids (may be NULL).  A request whose K or N exceeds
+ * its drone's caps, or whose scratch exceeds the whole pool, is refused with
+ * MPPI_ERR_NOT_ADMITTED (none of the n is queued then). */
+int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const float* x0s, const double* t0s,
+                       const int32_t* Ks, const int32_t* Ns, int64_t* ids_out);
+/* Admits and launches at most one batch if a slot is free; writes how many
+ * requests it launched (0 if none could be admitted). */
+int mppi_server_step(mppi_server s, int32_t* launched);
+/* Collects finished requests (up to cap) into out; writes their count. */
+int mppi_server_poll(mppi_server s, mppi_result_t* out, int32_t cap, int32_t* n_out);
+/* [0] queued, [1] in flight, [2] scratch bytes in use, [3] peak scratch
+ * bytes, [4] batches launched, [5] requests finished, [6] drones, [7] pool bytes. */
+int mppi_server_stats(mppi_server s, double out[8]);
+/* Exports one drone's controller state (the mppi_export_state layout). */
+int mppi_server_export_drone(mppi_server s, int32_t drone, void* buf, size_t* size);
+/* Waits for everything in flight, then frees all device memory. */
+int mppi_server_destroy(mppi_server s);
+
 /* Device memory the handle holds, bytes. */
 int mppi_device_bytes(mppi_handle h, size_t* bytes);
 /* Device memory a handle with these params would hold, bytes. */

@@ -236,10 +236,9 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
   return z;
 }
 
-void fill_desc(mppi_handle h) {
-  const mppi_model_t& m = h->model;
-  const mppi_params_t& p = h->params;
-  SolveDesc& d = h->hd;
+}  // namespace
+
+void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int nu, SolveDesc& d) {
   d.mass = m.mass;
   d.inv_mass = (float)(1.0 / (double)m.mass);
   d.gravity = m.gravity;
@@ -260,7 +259,7 @@ void fill_desc(mppi_handle h) {
   d.objective = p.objective;
   d.K = p.K;
   d.N = p.N;
-  d.nu = h->nu;
+  d.nu = nu;
   d.dt = p.dt;
   d.lambda = p.lambda;
   d.inv_lambda = (float)(1.0 / (double)p.lambda);
@@ -287,9 +286,16 @@ void fill_desc(mppi_handle h) {
   }
   for (int i = 0; i < 4; ++i) d.R[i] = p.R[i];
   d.hover = m.mass * m.gravity;
+}
+
+namespace {
+
+void fill_desc(mppi_handle h) {
+  fill_model_params(h->model, h->params, h->nu, h->hd);
+  SolveDesc& d = h->hd;
   d.N_cap = h->N_cap;
   d.block = h->block;
-  d.n_tiles = (p.K + h->block - 1) / h->block;
+  d.n_tiles = (h->params.K + h->block - 1) / h->block;
   d.ext_noise = 0;
 }
 

@@ -23,6 +23,8 @@ __host__ __device__ int path_fits_smem(int S);
 uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap);
 unsigned long long launches_so_far();
 void add_launches(int n);  // kernels run by a graph launch
+// model, sampling and cost fields of a descriptor from the C-ABI structs
+void fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int nu, SolveDesc& d);
 // records the message mppi_last_error() returns on this thread
 void set_last_error(const char* msg);
 // sets the dynamic shared-memory limit of every rollout kernel (once per device)

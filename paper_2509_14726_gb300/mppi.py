@@ -98,6 +98,15 @@ def load():
         "mppi_estimate_bytes": ([C.POINTER(Params), C.POINTER(TrackC), C.POINTER(sz)], C.c_int),
         "mppi_kernel_launches": ([], C.c_uint64),
         "mppi_abi_sizes": ([C.POINTER(sz)], C.c_int),
+        "mppi_clock": ([], C.c_double),
+        "mppi_server_create": ([I32, sz, I32, I32, C.POINTER(vp)], C.c_int),
+        "mppi_server_add_drone": ([vp, C.POINTER(Model), C.POINTER(Params), C.POINTER(TrackC), C.POINTER(I32)], C.c_int),
+        "mppi_server_submit": ([vp, I32, vp, vp, vp, vp, vp, vp], C.c_int),
+        "mppi_server_step": ([vp, C.POINTER(I32)], C.c_int),
+        "mppi_server_poll": ([vp, vp, I32, C.POINTER(I32)], C.c_int),
+        "mppi_server_stats": ([vp, C.POINTER(C.c_double)], C.c_int),
+        "mppi_server_export_drone": ([vp, I32, vp, C.POINTER(sz)], C.c_int),
+        "mppi_server_destroy": ([vp], C.c_int),
         "mppi_solve_noalloc": ([C.POINTER(Model), C.POINTER(Params), C.POINTER(TrackC), vp, C.c_double, vp, U32, I32,
                                 vp, vp, vp], C.c_int),
         "mppi_last_error": ([], C.c_char_p),
@@ -493,3 +502,83 @@ def encode_state(N_cap: int, nu: int, U, iter: int = 0, gate: int = 0, prevcnt=N
                       has_prev, int(has_theta), int(U.shape[0] if n_nom is None else n_nom), n_prev, int(gate), 0, 0, 0,
                       float(theta), float(v_theta), float(c_last), *[float(v) for v in x0], 0.0, 0.0, 0.0, 0.0)
     return struct.pack("<4I", 0x4D505049, 1, N_cap, nu) + dev + Uf.tobytes() + pc.tobytes()
+
+
+# ---------------------------------------------------------------------------
+# serving (continuous batching): thin wrappers of mppi_server_*
+# ---------------------------------------------------------------------------
+
+RESULT_DTYPE = np.dtype([("request", np.int64), ("drone", np.int32), ("status", np.int32), ("K", np.int32),
+                         ("N", np.int32), ("u0", np.float32, 5), ("t_submit", np.float64), ("t_launch", np.float64),
+                         ("t_done", np.float64)], align=True)
+
+
+def mppi_clock() -> float:
+    return float(load().mppi_clock())
+
+
+class Server:
+    """One mppi_server: resident state of many drones plus a scratch pool."""
+
+    def __init__(self, max_drones: int, budget_bytes: int, n_slots: int = 3, max_batch: int = 512):
+        h = C.c_void_p()
+        _check(load().mppi_server_create(int(max_drones), C.c_size_t(int(budget_bytes)), int(n_slots),
+                                         int(max_batch), C.byref(h)))
+        self.h = h.value
+        self._keep = []
+
+    def add_drone(self, mc, sc, track, K_cap: int, N_cap: int, block: int = 128) -> int:
+        tables = TrackArrays(track)
+        self._keep.append(tables)
+        d = I32()
+        _check(load().mppi_server_add_drone(C.c_void_p(self.h), C.byref(make_model(mc)),
+                                            C.byref(make_params(sc, block=block, N_cap=N_cap, K_cap=K_cap)),
+                                            C.byref(tables.c), C.byref(d)))
+        return int(d.value)
+
+    def submit(self, drones, x0s, t0s, Ks, Ns) -> np.ndarray:
+        n = len(drones)
+        dr = np.ascontiguousarray(drones, np.int32)
+        x = _f32(np.asarray(x0s).reshape(n, 13))
+        t = np.ascontiguousarray(t0s, np.float64)
+        k = np.ascontiguousarray(Ks, np.int32)
+        nn = np.ascontiguousarray(Ns, np.int32)
+        ids = np.zeros(n, np.int64)
+        _check(load().mppi_server_submit(C.c_void_p(self.h), n, dr.ctypes.data, x.ctypes.data, t.ctypes.data,
+                                         k.ctypes.data, nn.ctypes.data, ids.ctypes.data))
+        return ids
+
+    def step(self) -> int:
+        n = I32()
+        _check(load().mppi_server_step(C.c_void_p(self.h), C.byref(n)))
+        return int(n.value)
+
+    def poll(self, cap: int = 8192) -> np.ndarray:
+        out = np.zeros(cap, RESULT_DTYPE)
+        n = I32()
+        _check(load().mppi_server_poll(C.c_void_p(self.h), out.ctypes.data, int(cap), C.byref(n)))
+        return out[: n.value]
+
+    def stats(self) -> dict:
+        a = (C.c_double * 8)()
+        _check(load().mppi_server_stats(C.c_void_p(self.h), a))
+        keys = ("queued", "in_flight", "scratch_used", "scratch_peak", "batches", "finished", "drones", "pool")
+        return dict(zip(keys, list(a)))
+
+    def export_drone(self, d: int) -> bytes:
+        n = C.c_size_t(0)
+        _check(load().mppi_server_export_drone(C.c_void_p(self.h), int(d), None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().mppi_server_export_drone(C.c_void_p(self.h), int(d), C.cast(buf, C.c_void_p), C.byref(n)))
+        return buf.raw
+
+    def close(self):
+        if self.h:
+            _check(load().mppi_server_destroy(C.c_void_p(self.h)))
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
