@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--drones", type=int, default=256)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
 
@@ -243,11 +245,20 @@ def main():
     t0 = 0.3
     X0 = start_states(items, t0)
     from paper_2509_14726_gb300 import workloads as W
-    ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track) for it in items]
+    # ---- autotuning (untimed): block size and graph form of the batch plan ----
+    tuning = {"block": 128, "graph_mode": 1, "table": None}
+    if not args.no_tune:
+        from paper_2509_14726_gb300 import autotune as AT
+
+        def make_handles(block):
+            return [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=block) for it in items]
+
+        tuning = AT.tune_batch(make_handles, X0, t0, blocks=(64, 96, 128), modes=(1, 2), cache=None)
+    ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=tuning["block"]) for it in items]
     hs = [c.h for c in ctls]
     steps_per_solve = float(sum(it.K * it.N for it in items))
     flops = {o: sum(it.K * it.N * FLOPS_PER_STEP[o] for it in items if it.objective == o) for o in (0, 1, 2)}
-    plan = M.mppi_batch_create(hs, use_graph=True)
+    plan = M.mppi_batch_create(hs, use_graph=tuning["graph_mode"])
     stream = torch.cuda.Stream()
     d_x0 = torch.tensor(np.float32(X0), device="cuda")
     d_t0 = torch.full((len(items),), t0, dtype=torch.float64, device="cuda")
@@ -350,6 +361,25 @@ def main():
         c2.close()
         e2e["batched_vs_plain_solves_per_s"] = e2e["solves_per_s"] / plain["batch_one_solve_per_launch"]["solves_per_s"]
 
+    # ---- serving: a fleet at its own rates, continuous batching vs plain ----
+    serving_out = None
+    if not args.no_serving and rank == 0:
+        from paper_2509_14726_gb300 import serving as SV
+        fleet = W.c5_fleet(2000)
+        sched = SV.make_schedule(fleet, duration_s=2.0, time_scale=0.3, K_choices=[1024, 4096, 16384],
+                                 N_choices=[30, 50, 80], seed=0)
+        served = SV.run_served(fleet, sched, budget_bytes=40 << 30, n_slots=3, max_batch=512)
+        plain_s = SV.run_plain(fleet, sched, time_limit_s=3.0)
+        sub = fleet[:200]
+        sched_lo = SV.make_schedule(sub, duration_s=2.0, time_scale=0.1, K_choices=[1024, 4096, 16384],
+                                    N_choices=[30, 50, 80], seed=0)
+        serving_out = {
+            "fleet": "2000 drones at 50/100/200 Hz x 0.3 (Poisson-jittered), K in {1024,4096,16384}, "
+                     "N in {30,50,80}, 5-9 gate courses, 40 GB scratch budget, 2 s",
+            "served": served, "plain_one_solve_per_request": plain_s,
+            "low_load_200_drones_x0.1": {"served": SV.run_served(sub, sched_lo),
+                                         "plain": SV.run_plain(sub, sched_lo, time_limit_s=4.0)}}
+
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(items, args.cpu_sample_s)
@@ -367,7 +397,9 @@ def main():
                        "parallelism": f"dp{world} (drones sharded, no collective)"},
             "solves_per_s": len(items) * world / (ms_max / 1e3),
             "gpu_launches": int(launches),
-            "roofline": roofline, "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "clocks": clocks,
+            "roofline": roofline, "e2e": e2e, "plain": plain, "serving": serving_out,
+            "tuning": {"block": tuning["block"], "graph_mode": tuning["graph_mode"], "table": tuning["table"]},
+            "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     M.mppi_batch_destroy(plan)

@@ -1,0 +1,158 @@
+"""Autotuner for the solve's launch configuration.
+
+It times the library's real entry points with CUDA events (after warm-up, on
+the launching stream) over the knobs the kernels expose:
+
+* rollout block size (threads per tile): 32, 64, 96, 128 -- the rollout
+  kernel is built for 96 registers, five 128-thread blocks per SM;
+* for batch plans, the CUDA-graph form: one concurrent branch per
+  (objective, noise type, block) group, or one serial chain;
+* optionally the noise storage (float32 or bfloat16; bfloat16 changes the
+  numerics, so it is only searched when the caller allows it).
+
+Results are cached in a JSON file keyed by GPU name, objective, K bucket (next
+power of two) and N bucket (next multiple of 16).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import mppi as M
+from . import workloads as W
+
+BLOCKS = (32, 64, 96, 128)
+DEFAULT_CACHE = os.environ.get("MPPI_AUTOTUNE_CACHE",
+                               os.path.join(os.path.expanduser("~"), ".cache", "mppi_autotune.json"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_name() -> str:
+    torch = _torch()
+    return torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+
+
+def bucket_key(objective: int, K: int, N: int) -> str:
+    kb = 1 << max(0, math.ceil(math.log2(max(1, K))))
+    nb = 16 * math.ceil(max(1, N) / 16)
+    return f"{gpu_name()}|obj{objective}|K{kb}|N{nb}"
+
+
+class Cache:
+    def __init__(self, path: str = DEFAULT_CACHE):
+        self.path = path
+        self.data: Dict[str, dict] = {}
+        if path and os.path.exists(path):
+            try:
+                with open(path) as f:
+                    self.data = json.load(f)
+            except (OSError, ValueError):
+                self.data = {}
+
+    def get(self, key: str) -> Optional[dict]:
+        return self.data.get(key)
+
+    def put(self, key: str, value: dict) -> None:
+        self.data[key] = value
+        if self.path:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.data, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+
+def time_single(mc, sc, track, block: int, noise_dtype: int = M.NOISE_F32, reps: int = 20, warmup: int = 5,
+                x0=None, t0: float = 0.0) -> float:
+    """Mean device time (ms) of one mppi_solve_async with this block size."""
+    torch = _torch()
+    ctl = M.Controller(mc, sc, track, noise_dtype=noise_dtype, block=block)
+    x = x0 if x0 is not None else W.hover_state_before_gate(track.gates, 0, 1.0)
+    s = torch.cuda.Stream()
+    dx = torch.tensor(np.float32(x), device="cuda")
+    du = torch.zeros(5, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            M.mppi_solve_async(ctl.h, dx.data_ptr(), t0, s, du.data_ptr())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            M.mppi_solve_async(ctl.h, dx.data_ptr(), t0, s, du.data_ptr())
+        e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctl.close()
+    return ms
+
+
+def tune_single(mc, sc, track, blocks: Sequence[int] = BLOCKS, allow_bf16: bool = False,
+                cache: Optional[Cache] = None, x0=None, t0: float = 0.0) -> dict:
+    """Best block (and noise storage, if allowed) for one solve shape."""
+    key = bucket_key(sc.objective, sc.K, sc.N)
+    if cache is not None and cache.get(key):
+        return cache.get(key)
+    dtypes = (M.NOISE_F32, M.NOISE_BF16) if allow_bf16 else (M.NOISE_F32,)
+    table = []
+    for dt in dtypes:
+        for b in blocks:
+            table.append({"block": b, "noise_dtype": dt,
+                          "ms": time_single(mc, sc, track, b, dt, x0=x0, t0=t0)})
+    best = min(table, key=lambda r: r["ms"])
+    out = {"block": best["block"], "noise_dtype": best["noise_dtype"], "ms": best["ms"], "table": table}
+    if cache is not None:
+        cache.put(key, out)
+    return out
+
+
+def time_batch(make_handles: Callable[[int], List], x0s: np.ndarray, t0: float, mode: int, block: int,
+               reps: int = 10, warmup: int = 3) -> float:
+    """Mean device time (ms) of one batched solve (mppi_batch_solve_async)."""
+    torch = _torch()
+    ctls = make_handles(block)
+    plan = M.mppi_batch_create([c.h for c in ctls], use_graph=mode)
+    n = len(ctls)
+    s = torch.cuda.Stream()
+    dx = torch.tensor(np.float32(x0s), device="cuda")
+    dt = torch.full((n,), float(t0), dtype=torch.float64, device="cuda")
+    du = torch.zeros((n, 5), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            M.mppi_batch_solve_async(plan, dx.data_ptr(), dt.data_ptr(), s, du.data_ptr())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            M.mppi_batch_solve_async(plan, dx.data_ptr(), dt.data_ptr(), s, du.data_ptr())
+        e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    M.mppi_batch_destroy(plan)
+    for c in ctls:
+        c.close()
+    return ms
+
+
+def tune_batch(make_handles: Callable[[int], List], x0s: np.ndarray, t0: float,
+               blocks: Sequence[int] = BLOCKS, modes: Sequence[int] = (1, 2), cache: Optional[Cache] = None,
+               key: Optional[str] = None) -> dict:
+    """Best (block, graph form) for a batch; make_handles(block) builds the
+    batch's Controllers with that block size."""
+    full_key = f"{gpu_name()}|batch|{key}" if key else None
+    if cache is not None and full_key and cache.get(full_key):
+        return cache.get(full_key)
+    table = []
+    for b in blocks:
+        for m in modes:
+            table.append({"block": b, "graph_mode": m, "ms": time_batch(make_handles, x0s, t0, m, b)})
+    best = min(table, key=lambda r: r["ms"])
+    out = {"block": best["block"], "graph_mode": best["graph_mode"], "ms": best["ms"], "table": table}
+    if cache is not None and full_key:
+        cache.put(full_key, out)
+    return out
