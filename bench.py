@@ -151,6 +151,14 @@ def sum_over_ranks(world, v: float) -> float:
     return float(t.item())
 
 
+def aggregate(world: int, steps_this_rank: float, ms_this_rank: float):
+    """Whole-job throughput: all ranks' rollout steps over the slowest rank's
+    time per step.  Returns (value, ms_max, total_steps)."""
+    ms_max = max_over_ranks(world, ms_this_rank)
+    total = sum_over_ranks(world, steps_this_rank)
+    return total / (ms_max / 1e3), ms_max, total
+
+
 def workload(rank: int, n: int):
     from paper_2509_14726_gb300 import workloads as W
     return W.c3_batch(n_drones=n, seed=3 + 1000 * rank)
@@ -289,9 +297,7 @@ def main():
     clocks = sampler.stop()
     launches = M.mppi_kernel_launches() - launches0
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = max_over_ranks(world, ms)
-    total_steps = sum_over_ranks(world, steps_per_solve)
-    value = total_steps / (ms_max / 1e3)
+    value, ms_max, total_steps = aggregate(world, steps_per_solve, ms)
 
     # ---- end to end through the host API ----
     x0_host = np.float32(X0)
