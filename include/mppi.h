@@ -56,6 +56,11 @@ typedef enum {
 enum { MPPI_MODEL_CTBR = 0, MPPI_MODEL_ROTOR_RATE = 1 };
 enum { MPPI_OBJ_GATE = 0, MPPI_OBJ_CONTOUR = 1, MPPI_OBJ_TRACK = 2 };
 enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
+/* where the normals of Eq. 3 are drawn: a Philox pass before the rollout
+ * (stored, then loaded by the rollout), or inside the rollout itself (the
+ * same Philox / Box-Muller arithmetic, still stored for the update and the
+ * diagnostics).  Both give bit-identical noise. */
+enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1 };
 /* accumulation of the K-sample weighted update sum (Eq. 5) */
 enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
 enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };
@@ -109,6 +114,7 @@ typedef struct {
   int32_t block;         /* threads per block of the rollout (0 = 128) */
   int32_t N_cap;         /* largest N later solves may use (0 = N) */
   int32_t K_cap;         /* largest K later solves may use (0 = K) */
+  int32_t noise_gen;     /* MPPI_NOISEGEN_* */
 } mppi_params_t;
 
 /* Track: waypoints W, arc-length path P_arc and reference tau_ref

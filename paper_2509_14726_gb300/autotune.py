@@ -7,6 +7,8 @@ the launching stream) over the knobs the kernels expose:
   kernel is built for 96 registers, five 128-thread blocks per SM;
 * for batch plans, the CUDA-graph form: one concurrent branch per
   (objective, noise type, block) group, or one serial chain;
+* where the normals are drawn: a separate Philox pass or inside the rollout
+  (the same draws; the cheaper form depends on the shape);
 * optionally the noise storage (float32 or bfloat16; bfloat16 changes the
   numerics, so it is only searched when the caller allows it).
 
@@ -71,10 +73,10 @@ class Cache:
 
 
 def time_single(mc, sc, track, block: int, noise_dtype: int = M.NOISE_F32, reps: int = 20, warmup: int = 5,
-                x0=None, t0: float = 0.0) -> float:
+                x0=None, t0: float = 0.0, noise_gen: int = M.NOISEGEN_KERNEL) -> float:
     """Mean device time (ms) of one mppi_solve_async with this block size."""
     torch = _torch()
-    ctl = M.Controller(mc, sc, track, noise_dtype=noise_dtype, block=block)
+    ctl = M.Controller(mc, sc, track, noise_dtype=noise_dtype, block=block, noise_gen=noise_gen)
     x = x0 if x0 is not None else W.hover_state_before_gate(track.gates, 0, 1.0)
     s = torch.cuda.Stream()
     dx = torch.tensor(np.float32(x), device="cuda")
@@ -94,29 +96,33 @@ def time_single(mc, sc, track, block: int, noise_dtype: int = M.NOISE_F32, reps:
 
 
 def tune_single(mc, sc, track, blocks: Sequence[int] = BLOCKS, allow_bf16: bool = False,
-                cache: Optional[Cache] = None, x0=None, t0: float = 0.0) -> dict:
-    """Best block (and noise storage, if allowed) for one solve shape."""
+                cache: Optional[Cache] = None, x0=None, t0: float = 0.0,
+                noise_gens: Sequence[int] = (M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED)) -> dict:
+    """Best block, noise generation (and noise storage, if allowed) for one
+    solve shape."""
     key = bucket_key(sc.objective, sc.K, sc.N)
     if cache is not None and cache.get(key):
         return cache.get(key)
     dtypes = (M.NOISE_F32, M.NOISE_BF16) if allow_bf16 else (M.NOISE_F32,)
     table = []
     for dt in dtypes:
-        for b in blocks:
-            table.append({"block": b, "noise_dtype": dt,
-                          "ms": time_single(mc, sc, track, b, dt, x0=x0, t0=t0)})
+        for g in noise_gens:
+            for b in blocks:
+                table.append({"block": b, "noise_dtype": dt, "noise_gen": g,
+                              "ms": time_single(mc, sc, track, b, dt, x0=x0, t0=t0, noise_gen=g)})
     best = min(table, key=lambda r: r["ms"])
-    out = {"block": best["block"], "noise_dtype": best["noise_dtype"], "ms": best["ms"], "table": table}
+    out = {"block": best["block"], "noise_dtype": best["noise_dtype"], "noise_gen": best["noise_gen"],
+           "ms": best["ms"], "table": table}
     if cache is not None:
         cache.put(key, out)
     return out
 
 
-def time_batch(make_handles: Callable[[int], List], x0s: np.ndarray, t0: float, mode: int, block: int,
-               reps: int = 10, warmup: int = 3) -> float:
+def time_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float, mode: int, block: int,
+               reps: int = 10, warmup: int = 3, noise_gen: Optional[int] = None) -> float:
     """Mean device time (ms) of one batched solve (mppi_batch_solve_async)."""
     torch = _torch()
-    ctls = make_handles(block)
+    ctls = make_handles(block) if noise_gen is None else make_handles(block, noise_gen=noise_gen)
     plan = M.mppi_batch_create([c.h for c in ctls], use_graph=mode)
     n = len(ctls)
     s = torch.cuda.Stream()
@@ -139,20 +145,25 @@ def time_batch(make_handles: Callable[[int], List], x0s: np.ndarray, t0: float, 
     return ms
 
 
-def tune_batch(make_handles: Callable[[int], List], x0s: np.ndarray, t0: float,
+def tune_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float,
                blocks: Sequence[int] = BLOCKS, modes: Sequence[int] = (1, 2), cache: Optional[Cache] = None,
-               key: Optional[str] = None) -> dict:
-    """Best (block, graph form) for a batch; make_handles(block) builds the
-    batch's Controllers with that block size."""
+               key: Optional[str] = None, noise_gens: Optional[Sequence[int]] = None) -> dict:
+    """Best (block, graph form[, noise generation]) for a batch;
+    make_handles(block) builds the batch's Controllers with that block size
+    (make_handles(block, noise_gen=g) when noise_gens is given)."""
     full_key = f"{gpu_name()}|batch|{key}" if key else None
     if cache is not None and full_key and cache.get(full_key):
         return cache.get(full_key)
+    gens = list(noise_gens) if noise_gens else [None]
     table = []
-    for b in blocks:
-        for m in modes:
-            table.append({"block": b, "graph_mode": m, "ms": time_batch(make_handles, x0s, t0, m, b)})
+    for g in gens:
+        for b in blocks:
+            for m in modes:
+                table.append({"block": b, "graph_mode": m, "noise_gen": M.NOISEGEN_DEFAULT if g is None else g,
+                              "ms": time_batch(make_handles, x0s, t0, m, b, noise_gen=g)})
     best = min(table, key=lambda r: r["ms"])
-    out = {"block": best["block"], "graph_mode": best["graph_mode"], "ms": best["ms"], "table": table}
+    out = {"block": best["block"], "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
+           "ms": best["ms"], "table": table}
     if cache is not None and full_key:
         cache.put(full_key, out)
     return out

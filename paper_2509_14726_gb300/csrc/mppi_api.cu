@@ -133,7 +133,7 @@ struct mppi_batch_s {
   int n = 0;
   SolveDesc* d_descs = nullptr;
   struct Group {
-    int objective, bf16, block;
+    int objective, bf16, block, fused;
     uint32_t smem;
     int n_tiles;
     Tile* d_tiles;
@@ -184,6 +184,8 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   if (p->noise_dtype != MPPI_NOISE_F32 && p->noise_dtype != MPPI_NOISE_BF16)
     return fail(MPPI_ERR_ARG, "unknown noise dtype");
   if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
+  if (p->noise_gen != MPPI_NOISEGEN_KERNEL && p->noise_gen != MPPI_NOISEGEN_FUSED)
+    return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   int blk = p->block ? p->block : 128;
   if (blk < 32 || blk > rollout_max_block() || blk % 32)
     return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
@@ -266,6 +268,7 @@ void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int 
   d.seed = p.seed;
   d.drone_id = p.drone_id;
   d.noise_bf16 = p.noise_dtype == MPPI_NOISE_BF16;
+  d.noise_fused = p.noise_gen == MPPI_NOISEGEN_FUSED;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -558,13 +561,16 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
 
 static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   const SolveDesc& d = h->hd;
+  int gen = 0;  // caller noise is already stored: the rollout loads it
   if (h->ext_noise_pending) {
     h->ext_noise_pending = false;
+  } else if (d.noise_fused) {
+    gen = 1;
   } else {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s));
   }
   const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, h->block, merge_cap(d.n_tiles));
-  CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s));
+  CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen));
   return MPPI_OK;
 }
 
@@ -804,8 +810,8 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     const auto& g = b->rollout_groups[i];
     cudaStream_t bs = b->branch_streams[i];
     CU(cudaStreamWaitEvent(bs, b->fork, 0));
-    CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs));
+    if (!g.fused) CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.fused));
     CU(cudaEventRecord(b->join[i], bs));
     CU(cudaStreamWaitEvent(s, b->join[i], 0));
   }
@@ -815,7 +821,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s));
   for (const auto& g : b->rollout_groups)
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.fused));
   return MPPI_OK;
 }
 
@@ -853,9 +859,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->branches = use_graph == 1;
   // group tiles by launch configuration; longest horizons first (LPT)
   struct Key {
-    int obj, bf16, block;
+    int obj, bf16, block, fused;
     bool operator<(const Key& o) const {
-      return obj != o.obj ? obj < o.obj : bf16 != o.bf16 ? bf16 < o.bf16 : block < o.block;
+      return obj != o.obj ? obj < o.obj : bf16 != o.bf16 ? bf16 < o.bf16 : block != o.block ? block < o.block
+                                                                                           : fused < o.fused;
     }
   };
   std::vector<std::pair<Key, std::vector<Tile>>> rg;
@@ -872,8 +879,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
     const SolveDesc& d = hs[i]->hd;
-    Key k{d.objective, d.noise_bf16, d.block};
-    Key kn{0, d.noise_bf16, d.block};
+    Key k{d.objective, d.noise_bf16, d.block, d.noise_fused};
+    Key kn{0, d.noise_bf16, d.block, 0};
     auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
       for (size_t j = 0; j < v.size(); ++j)
         if (!(v[j].first < key) && !(key < v[j].first)) return (int)j;
@@ -883,10 +890,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     int gi = find(rg, k);
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
     rsmem[gi] = std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, d.block, merge_cap(d.n_tiles)));
-    int gn = find(ng, kn);
+    const int gn = d.noise_fused ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
       rg[gi].second.push_back(Tile{i, t * d.block});
-      ng[gn].second.push_back(Tile{i, t * d.block});
+      if (gn >= 0) ng[gn].second.push_back(Tile{i, t * d.block});
     }
     if (d.objective == MPPI_OBJ_GATE) which.push_back(i);
   }
@@ -917,7 +924,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     auto& v = rg[gi].second;
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
-    b->rollout_groups.push_back({rg[gi].first.obj, rg[gi].first.bf16, rg[gi].first.block, rsmem[gi], (int)v.size(), tp, tp});
+    const Key& k = rg[gi].first;
+    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.fused, rsmem[gi], (int)v.size(), tp, tp});
     tp += v.size();
   }
   for (auto& g : ng) {
@@ -939,8 +947,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   if (!which.empty() && cudaMemcpy(b->d_which, which.data(), sizeof(int32_t) * which.size(), cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "work list upload failed"));
   b->kernels_per_solve = (int)b->noise_groups.size() + (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
-  if (b->use_graph && b->branches && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8)
-    b->kernels_per_solve = 2 * (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
+  if (b->use_graph && b->branches && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8) {
+    b->kernels_per_solve = b->n_which > 0 ? 1 : 0;
+    for (const auto& g : b->rollout_groups) b->kernels_per_solve += g.fused ? 1 : 2;
+  }
   int rc = hostio_alloc(b->io, n);
   if (rc) return cleanup(rc);
   if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
@@ -1061,7 +1071,8 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
     for (int obj = 0; obj < 3; ++obj) {
       for (const auto& g : b->rollout_groups)
         if (g.objective == obj &&
-            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s) != cudaSuccess)
+            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.fused) !=
+                cudaSuccess)
           status = MPPI_ERR_CUDA;
       cudaEventRecord(ev[2 + obj], s);
     }

@@ -206,20 +206,54 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
   }
 }
 
-template <int BF16>
+// NC: read through the non-coherent (read-only) path; only for noise written
+// by an earlier kernel.  Noise this kernel wrote itself is read coherently.
+template <int BF16, bool NC = true>
 __device__ __forceinline__ void load_noise(const SolveDesc& d, size_t idx, float z[kNU], bool five) {
   if (BF16) {
-    const uint2 w = __ldg(d.Zb + idx);
+    const uint2 w = NC ? __ldg(d.Zb + idx) : d.Zb[idx];
     __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
     __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
     const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     z[0] = fa.x; z[1] = fa.y; z[2] = fb.x; z[3] = fb.y;
     z[4] = five ? __bfloat162float(d.Z5b[idx]) : 0.f;
   } else {
-    const float4 v = __ldg(d.Z4 + idx);
+    const float4 v = NC ? __ldg(d.Z4 + idx) : d.Z4[idx];
     z[0] = v.x; z[1] = v.y; z[2] = v.z; z[3] = v.w;
-    z[4] = five ? __ldg(d.Z5 + idx) : 0.f;
+    z[4] = five ? (NC ? __ldg(d.Z5 + idx) : d.Z5[idx]) : 0.f;
   }
+}
+
+// Generates the standard normals of (sample m, step k) with the noise
+// kernel's Philox / Box-Muller arithmetic, stores them (float32 or bfloat16)
+// for the epilogue and diagnostics, and returns the stored values.
+template <int BF16>
+__device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int m, int k, float z[kNU], bool five) {
+  const size_t idx = (size_t)k * d.K + m;
+  float4 v = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
+  float z5 = 0.f;
+  if (five) {
+    const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
+    z5 = box_muller(x5.x, x5.y).x;
+  }
+  if (BF16) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<uint32_t*>(&a);
+    w.y = *reinterpret_cast<uint32_t*>(&b);
+    d.Zb[idx] = w;
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    v = make_float4(fa.x, fa.y, fb.x, fb.y);
+    if (five) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(z5);
+      d.Z5b[idx] = h;
+      z5 = __bfloat162float(h);
+    }
+  } else {
+    d.Z4[idx] = v;
+    if (five) d.Z5[idx] = z5;
+  }
+  z[0] = v.x; z[1] = v.y; z[2] = v.z; z[3] = v.w; z[4] = z5;
 }
 
 // ---------------------------------------------------------------------------
@@ -300,7 +334,7 @@ __device__ __forceinline__ double part_value(double raw, int f64) {
 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
 
-template <int OBJ, int BF16>
+template <int OBJ, int BF16, int GEN>
 __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__ descs,
                                                             const Tile* __restrict__ tiles, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -513,12 +547,23 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
     // software pipeline: the next step's noise is in flight during this step
     float z[kNU], zn[kNU];
-    load_noise<BF16>(d, (size_t)m, zn, five);
+    // GEN: the normals are generated here (one step ahead) instead of being
+    // loaded from the noise kernel's output
+    const uint32_t iter = GEN ? st->iter : 0u;
+    if (GEN)
+      gen_noise<BF16>(d, iter, m, 0, zn, five);
+    else
+      load_noise<BF16>(d, (size_t)m, zn, five);
 #pragma unroll kRolloutUnroll
     for (int k = 0; k < N; ++k) {
 #pragma unroll
       for (int j = 0; j < kNU; ++j) z[j] = zn[j];
-      if (k + 1 < N) load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
+      if (k + 1 < N) {
+        if (GEN)
+          gen_noise<BF16>(d, iter, m, k + 1, zn, five);
+        else
+          load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
+      }
       const float* Uk = sU + kNU * k;
       const float u0 = clampf(Uk[0] + sg0 * z[0], lo0, hi0);
       const float u1 = clampf(Uk[1] + sg1 * z[1], lo1, hi1);
@@ -656,6 +701,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     d.J[m] = Jd;
     d.info[m] = passed | ((first + 1) << 16);
   }
+  // (with GEN the epilogue reads noise other threads of this block stored;
+  // the barriers inside block_min_d make those stores visible)
   const double m_t = block_min_d(valid ? Jd : INFINITY, red);
   float e = 0.f;
   if (valid && !isinf(m_t)) e = expf(-(float)(Jd - m_t) * d.inv_lambda);
@@ -677,7 +724,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     for (int i = lane; i < nvalid; i += 32) {
       const float w = sE[i];
       float zz[kNU];
-      load_noise<BF16>(d, (size_t)k * K + tile.m0 + i, zz, five);
+      load_noise<BF16, !GEN>(d, (size_t)k * K + tile.m0 + i, zz, five);
 #pragma unroll
       for (int j = 0; j < kNU; ++j) {
         if (j >= nu) break;
@@ -973,7 +1020,10 @@ cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles,
 
 template <int OBJ, int BF16>
 static cudaError_t configure_t() {
-  return cudaFuncSetAttribute(rollout_kernel<OBJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 cudaError_t configure_kernels() {
@@ -988,23 +1038,26 @@ cudaError_t configure_kernels() {
 
 template <int OBJ, int BF16>
 static cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
-                                    uint32_t smem, LaunchIO io, cudaStream_t s) {
+                                    uint32_t smem, LaunchIO io, cudaStream_t s, int gen) {
   (void)cudaGetLastError();
-  rollout_kernel<OBJ, BF16><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  if (gen)
+    rollout_kernel<OBJ, BF16, 1><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  else
+    rollout_kernel<OBJ, BF16, 0><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
-                           int block, uint32_t smem, LaunchIO io, cudaStream_t s) {
+                           int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen) {
   if (n_tiles <= 0) return cudaSuccess;
   switch (objective * 2 + (bf16 ? 1 : 0)) {
-    case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0>(descs, tiles, n_tiles, block, smem, io, s);
-    case 1: return launch_rollout_t<MPPI_OBJ_GATE, 1>(descs, tiles, n_tiles, block, smem, io, s);
-    case 2: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0>(descs, tiles, n_tiles, block, smem, io, s);
-    case 3: return launch_rollout_t<MPPI_OBJ_CONTOUR, 1>(descs, tiles, n_tiles, block, smem, io, s);
-    case 4: return launch_rollout_t<MPPI_OBJ_TRACK, 0>(descs, tiles, n_tiles, block, smem, io, s);
-    case 5: return launch_rollout_t<MPPI_OBJ_TRACK, 1>(descs, tiles, n_tiles, block, smem, io, s);
+    case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 1: return launch_rollout_t<MPPI_OBJ_GATE, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 2: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 3: return launch_rollout_t<MPPI_OBJ_CONTOUR, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 4: return launch_rollout_t<MPPI_OBJ_TRACK, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 5: return launch_rollout_t<MPPI_OBJ_TRACK, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
     default: return cudaErrorInvalidValue;
   }
 }

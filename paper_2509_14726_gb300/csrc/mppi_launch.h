@@ -35,7 +35,7 @@ int rollout_max_block();
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
                          cudaStream_t s);
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
-                           int block, uint32_t smem, LaunchIO io, cudaStream_t s);
+                           int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen);
 cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
                           uint32_t* out, cudaStream_t s);

@@ -133,6 +133,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (block < 32 || block > kMaxBlock || block % 32) return fail(MPPI_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
   if (p.K < 1 || p.N < 1 || p.N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K or N out of range");
   if (!(p.dt > 0) || !(p.lambda > 0)) return fail(MPPI_ERR_ARG, "dt and lambda must be positive");
+  if (p.noise_gen != MPPI_NOISEGEN_KERNEL && p.noise_gen != MPPI_NOISEGEN_FUSED)
+    return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return fail(MPPI_ERR_ARG, "noise dtype");
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.objective == MPPI_OBJ_GATE && (d_track->n_gates < 1 || !d_track->gates))
@@ -188,6 +190,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.seed = p.seed;
   d.drone_id = p.drone_id;
   d.noise_bf16 = bf16;
+  d.noise_fused = p.noise_gen == MPPI_NOISEGEN_FUSED;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -250,7 +253,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, block);
   add_launches(2);
   if (cudaGetLastError() != cudaSuccess) return fail(MPPI_ERR_CUDA, "set-up kernel launch failed");
-  if (launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s) != cudaSuccess)
+  if (!d.noise_fused && launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "noise kernel launch failed");
   LaunchIO io;
   memset(&io, 0, sizeof io);
@@ -260,7 +263,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.u0 = d_u0;
   io.status = nullptr;
   const uint32_t smem = rollout_smem_bytes(p.N, p.objective, d.S, block, d.n_tiles > 32 ? d.n_tiles : 32);
-  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s) != cudaSuccess)
+  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_fused) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");
   return MPPI_OK;
 }

@@ -508,7 +508,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   // tiles: rollout groups by (objective, noise type, block), longest
   // horizons first; the noise launches reuse the same tiles per (type, block)
   struct Group {
-    int obj, bf16, block;
+    int obj, bf16, block, fused;
     std::vector<Tile> t;
     uint32_t smem = 0;
   };
@@ -521,9 +521,11 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     const SolveDesc& dd = hdesc[i];
     int g = -1;
     for (size_t q = 0; q < groups.size(); ++q)
-      if (groups[q].obj == dd.objective && groups[q].bf16 == dd.noise_bf16 && groups[q].block == dd.block) g = (int)q;
+      if (groups[q].obj == dd.objective && groups[q].bf16 == dd.noise_bf16 && groups[q].block == dd.block &&
+          groups[q].fused == dd.noise_fused)
+        g = (int)q;
     if (g < 0) {
-      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, {}, 0});
+      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_fused, {}, 0});
       g = (int)groups.size() - 1;
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * dd.block});
@@ -552,10 +554,11 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   io.u0 = sl.d_u0;
   io.status = sl.d_status;
   for (size_t q = 0; q < groups.size(); ++q)
-    SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm));
+    if (!groups[q].fused)
+      SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm));
   for (size_t q = 0; q < groups.size(); ++q)
     SCU(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
-                       groups[q].block, groups[q].smem, io, stm));
+                       groups[q].block, groups[q].smem, io, stm, groups[q].fused));
   SCU(launch_nominal(ddesc, reinterpret_cast<const int32_t*>(sl.dev + st.which), (int)which.size(), stm));
   SCU(cudaEventRecord(sl.done, stm));
   sl.reqs.swap(batch);

@@ -20,6 +20,8 @@ LIB_PATH = os.environ.get("MPPI_LIB") or os.path.join(HERE, "lib", "libmppi.so")
 
 MPPI_OK, MPPI_ERR_ARG, MPPI_ERR_OOM, MPPI_ERR_CUDA, MPPI_ERR_TIMEOUT, MPPI_ERR_NOT_ADMITTED, MPPI_WARN_DEGENERATE = range(7)
 NOISE_F32, NOISE_BF16 = 0, 1
+NOISEGEN_KERNEL, NOISEGEN_FUSED = 0, 1
+NOISEGEN_DEFAULT = NOISEGEN_KERNEL
 ACC_KAHAN32, ACC_F64, ACC_F32 = 0, 1, 2
 F = C.c_float
 I32 = C.c_int32
@@ -44,7 +46,7 @@ class Params(C.Structure):
                 ("temporal_rule", I32), ("q_lag", F), ("q_cont", F), ("q_omega", F * 3), ("r_dv", F),
                 ("r_dthrust", F), ("mu", F), ("v_theta_max", F), ("theta_back", F), ("theta_ahead", F),
                 ("Q", F * 13), ("QN", F * 13), ("R", F * 4), ("noise_dtype", I32), ("accum", I32), ("block", I32),
-                ("N_cap", I32), ("K_cap", I32)]
+                ("N_cap", I32), ("K_cap", I32), ("noise_gen", I32)]
 
 
 class TrackC(C.Structure):
@@ -159,7 +161,7 @@ def make_model(mc: W.ModelConfig) -> Model:
 
 
 def make_params(sc: W.SolveConfig, noise_dtype: int = NOISE_F32, accum: int = ACC_KAHAN32, block: int = 128,
-                N_cap: int = 0, K_cap: int = 0) -> Params:
+                N_cap: int = 0, K_cap: int = 0, noise_gen: Optional[int] = None) -> Params:
     p = Params()
     p.objective, p.K, p.N = sc.objective, sc.K, sc.N
     p.dt, p.lam = sc.dt, sc.lam
@@ -174,6 +176,7 @@ def make_params(sc: W.SolveConfig, noise_dtype: int = NOISE_F32, accum: int = AC
     p.QN[:] = list(sc.QN)
     p.R[:] = list(sc.R)
     p.noise_dtype, p.accum, p.block, p.N_cap, p.K_cap = noise_dtype, accum, block, N_cap, K_cap
+    p.noise_gen = NOISEGEN_DEFAULT if noise_gen is None else noise_gen
     return p
 
 
@@ -397,10 +400,11 @@ class Controller:
     """Owns one libmppi handle for one drone."""
 
     def __init__(self, mc: W.ModelConfig, sc: W.SolveConfig, track: W.Track, noise_dtype: int = NOISE_F32,
-                 accum: int = ACC_KAHAN32, block: int = 128, N_cap: int = 0, K_cap: int = 0):
+                 accum: int = ACC_KAHAN32, block: int = 128, N_cap: int = 0, K_cap: int = 0,
+                 noise_gen: Optional[int] = None):
         self.mc, self.sc, self.track = mc, sc, track
         self.model = make_model(mc)
-        self.params = make_params(sc, noise_dtype, accum, block, N_cap, K_cap)
+        self.params = make_params(sc, noise_dtype, accum, block, N_cap, K_cap, noise_gen)
         self.tables = TrackArrays(track)
         self.h = mppi_create(self.model, self.params, self.tables)
         self.K, self.N = sc.K, sc.N
@@ -527,12 +531,13 @@ class Server:
         self.h = h.value
         self._keep = []
 
-    def add_drone(self, mc, sc, track, K_cap: int, N_cap: int, block: int = 128) -> int:
+    def add_drone(self, mc, sc, track, K_cap: int, N_cap: int, block: int = 128, noise_gen: Optional[int] = None) -> int:
         tables = TrackArrays(track)
         self._keep.append(tables)
         d = I32()
         _check(load().mppi_server_add_drone(C.c_void_p(self.h), C.byref(make_model(mc)),
-                                            C.byref(make_params(sc, block=block, N_cap=N_cap, K_cap=K_cap)),
+                                            C.byref(make_params(sc, block=block, N_cap=N_cap, K_cap=K_cap,
+                                                                noise_gen=noise_gen)),
                                             C.byref(tables.c), C.byref(d)))
         return int(d.value)
 

@@ -1,0 +1,201 @@
+"""Noise drawn inside the rollout (MPPI_NOISEGEN_FUSED) against the separate
+Philox pass and against the FP64 oracle.
+
+The fused rollout evaluates the same Philox4x32-10 / Box-Muller arithmetic on
+the same counters (Sec. III-B, Eq. 3), so the stored noise is bit-identical
+to the two-kernel path's.  The rest of the rollout is a separate compilation
+whose floating-point contractions the compiler chooses on its own, so costs
+and the update agree to binary32 rounding (observed: 1e-8 relative in J),
+not bit for bit; the same mode is bit-exact between the single, batched and
+served paths.  Against the oracle the fused path is held to the parity
+tolerances.  Covered: every objective, both noise storages, ragged tiles,
+consecutive solves (the iteration counter moves), the batched launch (all
+graph forms, both modes mixed in one plan), the server and caller noise (the
+allocation-free entry point is covered in its own file).
+"""
+import numpy as np
+import pytest
+
+from paper_2509_14726_gb300 import workloads as W
+from parity_util import U_ABS_TOL, compare, f32_case, make_pair
+
+# costs of the two compilations: binary32 rounding of a 13..50-step sum
+J_ROUND_TOL = 1e-6
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    torch.cuda.set_device(0)
+    from paper_2509_14726_gb300 import mppi
+    return mppi
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def _case(objective, K, N, seed=7):
+    mc, sc, tr, x0 = W.c2_full_scale(objective, seed)
+    sc.K, sc.N = K, N
+    return f32_case(mc, sc, tr, x0)
+
+
+def _x0(O, case, t0):
+    if case.sc.objective == 2:
+        x = np.float32(O.ref_eval(case.tr, t0)).astype(np.float64)
+        x[0:3] += 0.1
+        return x
+    return case.x0
+
+
+def _same(a, b):
+    np.testing.assert_array_equal(a.costs(), b.costs())
+    np.testing.assert_array_equal(a.unew(), b.unew())
+    np.testing.assert_array_equal(a.nominal(), b.nominal())
+    np.testing.assert_array_equal(a.noise(), b.noise())
+    assert a.export_state() == b.export_state()
+
+
+def _close(a, b):
+    """Same noise bit for bit; costs and update to binary32 rounding."""
+    np.testing.assert_array_equal(a.noise(), b.noise())
+    na, fa = a.sample_info()
+    nb, fb = b.sample_info()
+    same = (na == nb) & (fa == fb)
+    assert same.mean() >= 0.999
+    Ja, Jb = a.costs(), b.costs()
+    rel = np.abs(Ja - Jb) / np.maximum(np.abs(Jb), 1e-30)
+    assert rel[same].max() <= J_ROUND_TOL, rel.max()
+    assert np.abs(a.unew() - b.unew()).max() <= U_ABS_TOL
+    assert np.abs(a.nominal() - b.nominal()).max() <= U_ABS_TOL
+
+
+@pytest.mark.parametrize("objective", [0, 1, 2])
+@pytest.mark.parametrize("bf16", [0, 1])
+@pytest.mark.parametrize("K,N,block", [(1000, 13, 128), (3001, 20, 64), (33, 3, 32)])
+def test_fused_matches_separate(O, M, objective, bf16, K, N, block):
+    case = _case(objective, K, N)
+    kw = dict(noise_dtype=bf16, block=block)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_FUSED, **kw)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL, **kw)
+    t0 = 0.37
+    x0 = _x0(O, case, t0)
+    for rep in range(3):
+        ua, _ = a.solve(x0, t0 + 0.02 * rep)
+        ub, _ = b.solve(x0, t0 + 0.02 * rep)
+        assert np.abs(ua - ub).max() <= U_ABS_TOL
+        _close(a, b)
+        assert a.info()[2] == b.info()[2] == rep + 1
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("objective", [0, 1, 2])
+def test_fused_against_oracle(O, M, objective):
+    case = _case(objective, 4096, 50)
+    gpu, ora = make_pair(case, noise_gen=M.NOISEGEN_FUSED)
+    t0 = 0.37
+    x0 = _x0(O, case, t0)
+    gpu.solve(x0, t0)
+    r = ora.solve(x0, t0)
+    compare(gpu, r, f"fused noise, objective {objective}")
+    # the stored normals are the oracle's Philox / Box-Muller draws
+    Zg = gpu.noise()
+    ms = range(0, case.sc.K, 257)
+    zo = np.array([[O.normals4(case.sc.seed, case.sc.drone_id, m, k, 0, 0) for m in ms] for k in range(case.sc.N)])
+    assert np.max(np.abs(Zg[:, ::257, :4] - zo)) <= 6 * 2.0 ** -23 * np.max(np.abs(zo)) + 1e-6
+    gpu.close()
+
+
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
+def test_batch_with_mixed_noise_modes(M, use_graph):
+    """A plan holding fused and separate-noise handles of every objective
+    gives each solve exactly what it gets alone in the same mode."""
+    items = W.c3_batch(n_drones=8, K_lo=300, K_hi=3000, N_lo=5, N_hi=40)
+    trip = []
+    for i, it in enumerate(items):
+        sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id)
+        case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
+        mode = M.NOISEGEN_FUSED if i % 2 == 0 else M.NOISEGEN_KERNEL
+        g1 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
+        g2 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
+        trip.append((g1, g2, case))
+    X0 = np.array([c.x0 for _, _, c in trip])
+    t0 = np.full(len(trip), 0.3)
+    b = M.mppi_batch_create([g1.h for g1, _, _ in trip], use_graph=use_graph)
+    for rep in range(2):
+        ub, _ = M.mppi_batch_solve(b, len(trip), X0, t0)
+        for i, (g1, g2, c) in enumerate(trip):
+            ua, _ = g2.solve(c.x0, 0.3)
+            np.testing.assert_array_equal(ub[i], ua)
+            _same(g1, g2)
+    M.mppi_batch_destroy(b)
+    for g1, g2, _ in trip:
+        g1.close()
+        g2.close()
+
+
+def test_server_with_fused_noise(M):
+    fleet = W.c5_fleet(n_drones=6, distinct_tracks=4)
+    srv = M.Server(len(fleet), 1 << 30, n_slots=2, max_batch=4)
+    alone = []
+    for i, d in enumerate(fleet):
+        sc = W.SolveConfig(objective=d.objective, K=1024, N=30, dt=0.02, drone_id=d.drone_id)
+        mode = M.NOISEGEN_FUSED if i % 3 else M.NOISEGEN_KERNEL
+        srv.add_drone(W.ModelConfig(), sc, d.track, 2048, 30, noise_gen=mode)
+        alone.append(M.Controller(W.ModelConfig(), sc, d.track, K_cap=2048, N_cap=30, noise_gen=mode))
+    X0 = np.array([d.x0 for d in fleet])
+    n = len(fleet)
+    for rnd in range(2):
+        ids = srv.submit(np.arange(n), X0, np.full(n, 0.1 * rnd), np.full(n, 2048), np.full(n, 30))
+        got = {}
+        while len(got) < n:
+            while srv.step() > 0:
+                pass
+            for r in srv.poll().tolist():
+                got[int(r[0])] = r
+        for i, c in enumerate(alone):
+            c.set_shape(2048, 30)
+            u, _ = c.solve(X0[i], 0.1 * rnd)
+            np.testing.assert_array_equal(np.asarray(got[int(ids[i])][5], np.float32), u)
+    for i, c in enumerate(alone):
+        assert srv.export_drone(i) == c.export_state()
+        c.close()
+    srv.close()
+
+
+def test_caller_noise_on_a_fused_handle(M):
+    """mppi_set_noise on a fused handle: that solve uses the caller's normals
+    (the rollout loads them, as the separate path does), the next one draws
+    its own again."""
+    case = _case(0, 2048, 40)
+    rng = np.random.default_rng(5)
+    z = torch.tensor(rng.standard_normal((40, 2048, 4)).astype(np.float32), device="cuda").contiguous()
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_FUSED)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL)
+    for c in (a, b):
+        M.mppi_set_noise(c.h, z.data_ptr(), None)
+    for rep in range(2):
+        ua, _ = a.solve(case.x0, 0.0)
+        ub, _ = b.solve(case.x0, 0.0)
+        if rep == 0:
+            # both ran the loading kernel on the same normals
+            np.testing.assert_array_equal(ua, ub)
+            np.testing.assert_array_equal(a.costs(), b.costs())
+            np.testing.assert_array_equal(a.noise()[:, :, :4], z.cpu().numpy())
+        else:
+            assert np.abs(ua - ub).max() <= U_ABS_TOL
+            _close(a, b)
+    a.close()
+    b.close()

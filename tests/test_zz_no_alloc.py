@@ -92,3 +92,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(M):
                                      C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()))
     assert rc == M.MPPI_ERR_ARG
     assert b"static maximum" in M.load().mppi_last_error()
+
+
+def test_noalloc_fused_noise_equals_separate_pass(M):
+    """Noise drawn inside the rollout gives the two-kernel result to binary32
+    rounding (the noise is bit-identical; the rollout is another compilation)."""
+    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_CONTOUR)
+    sc.K, sc.N = 3000, 40
+    mc, sc, tr = W.f32_model(mc), W.f32_solve(sc), tr.as_f32()
+    d_track, keep = _device_track(M, tr)
+    model = M.make_model(mc)
+    d_x0 = torch.tensor(np.float32(x0), device="cuda")
+    d_U = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
+    d_U[:, 0] = float(np.float32(mc.mass) * np.float32(mc.gravity))
+    out = []
+    for mode in (M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED):
+        p = M.make_params(sc, noise_gen=mode)
+        d_Unew = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
+        d_u0 = torch.zeros(5, dtype=torch.float32, device="cuda")
+        M.mppi_solve_noalloc(model, p, d_track, d_x0.data_ptr(), 0.0, d_U.data_ptr(), 3, 0, None,
+                             d_Unew.data_ptr(), d_u0.data_ptr())
+        torch.cuda.synchronize()
+        out.append((d_u0.cpu().numpy(), d_Unew.cpu().numpy()))
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= U_TOL
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= U_TOL
