@@ -44,6 +44,33 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_STEP = {0: 423.0, 1: 491.0, 2: 478.0}
 
 
+def measured_traffic(steps_by_objective):
+    """DRAM bytes of the three rollout launches of one step, from the ncu
+    capture recorded under profiles/ (bytes per rollout step per objective,
+    scaled by this workload's K x N), or None when the kernel source is not
+    the one that was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_2509_14726_gb300", "csrc")
+    try:
+        with open(path) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+        h = hashlib.sha256()
+        for name in ("mppi_kernels.cu", "mppi_device.cuh"):
+            with open(os.path.join(src, name), "rb") as f:
+                h.update(f.read())
+    except OSError:
+        return None
+    rec = {ln[0]: ln[1:] for ln in lines if ln[0] == "source_sha256"}
+    if rec.get("source_sha256", [None])[0] != h.hexdigest():
+        return None
+    per = {ln[1]: float(ln[2]) for ln in lines if ln[0] == "bytes_per_step"}
+    names = {0: "gate", 1: "contour", 2: "track"}
+    if any(names[o] not in per for o in (0, 1, 2)):
+        return None
+    return sum(per[names[o]] * steps_by_objective[o] for o in (0, 1, 2))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,8 +352,12 @@ def main():
     roll_flops = flops[0] + flops[1] + flops[2]
     peak = n_sm * 128 * 2 * 2070e6 / 1e12
     achieved = roll_flops / (roll_ms / 1e3) / 1e12
+    steps_by_obj = {o: sum(it.K * it.N for it in items if it.objective == o) for o in (0, 1, 2)}
+    traffic = measured_traffic(steps_by_obj)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "rollout_kernel (3 launches, one per objective)",
+                "traffic": traffic, "kernel": "rollout_kernel (3 launches, one per objective)",
+                "traffic_note": "DRAM bytes of the 3 launches: ncu per-step figures of the 32-drone capture "
+                                "scaled by this batch's K x N (null if the kernel source changed since)",
                 "peak_note": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 x 2070 MHz (max SM clock)",
                 "phase_ms": {"noise": float(prof[0]), "rollout_gate": float(prof[1]),
                              "rollout_contour": float(prof[2]), "rollout_track": float(prof[3]),
