@@ -290,7 +290,7 @@ def main():
                     for it in items]
 
         tuning = AT.tune_batch(make_handles, X0, t0, blocks=(64, 96, 128), modes=(1, 2), cache=None,
-                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED))
+                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN))
     ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=tuning["block"], noise_gen=tuning["noise_gen"])
             for it in items]
     hs = [c.h for c in ctls]

@@ -56,11 +56,16 @@ typedef enum {
 enum { MPPI_MODEL_CTBR = 0, MPPI_MODEL_ROTOR_RATE = 1 };
 enum { MPPI_OBJ_GATE = 0, MPPI_OBJ_CONTOUR = 1, MPPI_OBJ_TRACK = 2 };
 enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
-/* where the normals of Eq. 3 are drawn: a Philox pass before the rollout
- * (stored, then loaded by the rollout), or inside the rollout itself (the
- * same Philox / Box-Muller arithmetic, still stored for the update and the
- * diagnostics).  Both give bit-identical noise. */
-enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1 };
+/* where the normals of Eq. 3 are drawn, all with the same Philox /
+ * Box-Muller arithmetic on the same counters (bit-identical draws):
+ *   KERNEL: a Philox pass before the rollout stores them; the rollout loads
+ *           them, and the update (Eq. 5) loads them again;
+ *   FUSED:  the rollout draws them itself and stores them for the update and
+ *           the diagnostics;
+ *   REGEN:  the rollout draws them and the update draws them again; nothing
+ *           is stored (no noise memory: mppi_get_noise / mppi_set_noise
+ *           return MPPI_ERR_ARG; needs MPPI_NOISE_F32). */
+enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1, MPPI_NOISEGEN_REGEN = 2 };
 /* accumulation of the K-sample weighted update sum (Eq. 5) */
 enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
 enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };
@@ -299,7 +304,8 @@ int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t* params, c
  * drones (each with its own K and N, up to the drone's caps) queue on the
  * host; mppi_server_step admits queued requests in arrival order while their
  * scratch (noise, costs, tile partials: about 16 K N bytes each, 20 K N for
- * contouring) fits in the pool's free space, and launches them as one batch
+ * contouring; about 12 K + 40 N K/block bytes with MPPI_NOISEGEN_REGEN)
+ * fits in the pool's free space, and launches them as one batch
  * (the kernels of mppi_solve_batch) on the next free stream slot, so batches
  * overlap on the device while later requests keep arriving.  A drone has at
  * most one request in flight; its next request waits for the previous one.

@@ -7,8 +7,9 @@ the launching stream) over the knobs the kernels expose:
   kernel is built for 96 registers, five 128-thread blocks per SM;
 * for batch plans, the CUDA-graph form: one concurrent branch per
   (objective, noise type, block) group, or one serial chain;
-* where the normals are drawn: a separate Philox pass or inside the rollout
-  (the same draws; the cheaper form depends on the shape);
+* where the normals are drawn: a separate Philox pass, inside the rollout
+  (stored), or inside the rollout and again in the update (never stored:
+  no noise memory); the same draws in every form;
 * optionally the noise storage (float32 or bfloat16; bfloat16 changes the
   numerics, so it is only searched when the caller allows it).
 
@@ -97,7 +98,7 @@ def time_single(mc, sc, track, block: int, noise_dtype: int = M.NOISE_F32, reps:
 
 def tune_single(mc, sc, track, blocks: Sequence[int] = BLOCKS, allow_bf16: bool = False,
                 cache: Optional[Cache] = None, x0=None, t0: float = 0.0,
-                noise_gens: Sequence[int] = (M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED)) -> dict:
+                noise_gens: Sequence[int] = (M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN)) -> dict:
     """Best block, noise generation (and noise storage, if allowed) for one
     solve shape."""
     key = bucket_key(sc.objective, sc.K, sc.N)
@@ -107,6 +108,8 @@ def tune_single(mc, sc, track, blocks: Sequence[int] = BLOCKS, allow_bf16: bool 
     table = []
     for dt in dtypes:
         for g in noise_gens:
+            if g == M.NOISEGEN_REGEN and dt != M.NOISE_F32:
+                continue  # regenerated noise is never stored, so it has no bfloat16 form
             for b in blocks:
                 table.append({"block": b, "noise_dtype": dt, "noise_gen": g,
                               "ms": time_single(mc, sc, track, b, dt, x0=x0, t0=t0, noise_gen=g)})

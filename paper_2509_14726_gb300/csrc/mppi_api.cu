@@ -133,7 +133,7 @@ struct mppi_batch_s {
   int n = 0;
   SolveDesc* d_descs = nullptr;
   struct Group {
-    int objective, bf16, block, fused;
+    int objective, bf16, block, gen;  // gen: MPPI_NOISEGEN_*
     uint32_t smem;
     int n_tiles;
     Tile* d_tiles;
@@ -184,8 +184,10 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   if (p->noise_dtype != MPPI_NOISE_F32 && p->noise_dtype != MPPI_NOISE_BF16)
     return fail(MPPI_ERR_ARG, "unknown noise dtype");
   if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
-  if (p->noise_gen != MPPI_NOISEGEN_KERNEL && p->noise_gen != MPPI_NOISEGEN_FUSED)
+  if (p->noise_gen < MPPI_NOISEGEN_KERNEL || p->noise_gen > MPPI_NOISEGEN_REGEN)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
+  if (p->noise_gen == MPPI_NOISEGEN_REGEN && p->noise_dtype != MPPI_NOISE_F32)
+    return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
   int blk = p->block ? p->block : 128;
   if (blk < 32 || blk > rollout_max_block() || blk % 32)
     return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
@@ -214,6 +216,7 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
   const int Gn = 2 * sq + 16;  // >= n_groups_for(T) for every T <= T_cap
   const bool bf16 = p->noise_dtype == MPPI_NOISE_BF16;
   const bool five = p->objective == MPPI_OBJ_CONTOUR;
+  const bool stored = p->noise_gen != MPPI_NOISEGEN_REGEN;
   Slab s;
   Sizes z;
   z.off_desc = s.take(sizeof(SolveDesc));
@@ -223,8 +226,8 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
   z.off_gates = s.take(sizeof(float) * 6 * std::max(1, t->n_gates));
   z.off_path = s.take(sizeof(float) * 6 * std::max(1, t->S) + 64);
   z.off_ref = s.take(sizeof(float) * 13 * std::max(1, t->T));
-  z.off_Z = s.take((size_t)N_cap * K_cap * (bf16 ? 8 : 16));
-  z.off_Z5 = s.take(five ? (size_t)N_cap * K_cap * (bf16 ? 2 : 4) : 16);
+  z.off_Z = s.take(stored ? (size_t)N_cap * K_cap * (bf16 ? 8 : 16) : 16);
+  z.off_Z5 = s.take(five && stored ? (size_t)N_cap * K_cap * (bf16 ? 2 : 4) : 16);
   z.off_J = s.take(sizeof(double) * K_cap);
   z.off_info = s.take(sizeof(int32_t) * K_cap);
   z.off_pm = s.take(sizeof(double) * (T_cap + Gn + 1));
@@ -268,7 +271,7 @@ void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int 
   d.seed = p.seed;
   d.drone_id = p.drone_id;
   d.noise_bf16 = p.noise_dtype == MPPI_NOISE_BF16;
-  d.noise_fused = p.noise_gen == MPPI_NOISEGEN_FUSED;
+  d.noise_gen = p.noise_gen;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -458,11 +461,11 @@ int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mp
   d.ref = reinterpret_cast<float*>(b + z.off_ref);
   d.T = track->T;
   d.dt_ref = track->dt_ref;
-  const bool bf16 = d.noise_bf16;
-  d.Z4 = bf16 ? nullptr : reinterpret_cast<float4*>(b + z.off_Z);
-  d.Zb = bf16 ? reinterpret_cast<uint2*>(b + z.off_Z) : nullptr;
-  d.Z5 = (!bf16 && h->nu == 5) ? reinterpret_cast<float*>(b + z.off_Z5) : nullptr;
-  d.Z5b = (bf16 && h->nu == 5) ? reinterpret_cast<__nv_bfloat16*>(b + z.off_Z5) : nullptr;
+  const bool bf16 = d.noise_bf16, stored = d.noise_gen != MPPI_NOISEGEN_REGEN;
+  d.Z4 = (stored && !bf16) ? reinterpret_cast<float4*>(b + z.off_Z) : nullptr;
+  d.Zb = (stored && bf16) ? reinterpret_cast<uint2*>(b + z.off_Z) : nullptr;
+  d.Z5 = (stored && !bf16 && h->nu == 5) ? reinterpret_cast<float*>(b + z.off_Z5) : nullptr;
+  d.Z5b = (stored && bf16 && h->nu == 5) ? reinterpret_cast<__nv_bfloat16*>(b + z.off_Z5) : nullptr;
   d.J = reinterpret_cast<double*>(b + z.off_J);
   d.info = reinterpret_cast<int32_t*>(b + z.off_info);
   d.part_m = reinterpret_cast<double*>(b + z.off_pm);
@@ -564,8 +567,8 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   int gen = 0;  // caller noise is already stored: the rollout loads it
   if (h->ext_noise_pending) {
     h->ext_noise_pending = false;
-  } else if (d.noise_fused) {
-    gen = 1;
+  } else if (d.noise_gen != MPPI_NOISEGEN_KERNEL) {
+    gen = d.noise_gen;
   } else {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s));
   }
@@ -643,6 +646,7 @@ int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass) {
 int mppi_get_noise(mppi_handle h, float* Z) {
   if (!h || !Z) return fail(MPPI_ERR_ARG, "null argument");
   const SolveDesc& d = h->hd;
+  if (d.noise_gen == MPPI_NOISEGEN_REGEN) return fail(MPPI_ERR_ARG, "regenerated noise is not stored");
   const size_t nk = (size_t)d.N * d.K;
   std::vector<float> z4(nk * 4), z5(h->nu == 5 ? nk : 0);
   if (d.noise_bf16) {
@@ -753,6 +757,7 @@ int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* strea
   if (h->nu == 5 && !d_Z5) return fail(MPPI_ERR_ARG, "contouring needs the 5th noise column");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SolveDesc& d = h->hd;
+  if (d.noise_gen == MPPI_NOISEGEN_REGEN) return fail(MPPI_ERR_ARG, "a regenerating handle has no noise buffer");
   const size_t nk = (size_t)d.N * d.K;
   const size_t el = d.noise_bf16 ? 2 : 4;
   CU(cudaMemcpyAsync(d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4, d_Z, nk * 4 * el, cudaMemcpyDeviceToDevice, s));
@@ -810,8 +815,8 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     const auto& g = b->rollout_groups[i];
     cudaStream_t bs = b->branch_streams[i];
     CU(cudaStreamWaitEvent(bs, b->fork, 0));
-    if (!g.fused) CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.fused));
+    if (g.gen == MPPI_NOISEGEN_KERNEL) CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen));
     CU(cudaEventRecord(b->join[i], bs));
     CU(cudaStreamWaitEvent(s, b->join[i], 0));
   }
@@ -821,7 +826,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s));
   for (const auto& g : b->rollout_groups)
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.fused));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen));
   return MPPI_OK;
 }
 
@@ -859,10 +864,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->branches = use_graph == 1;
   // group tiles by launch configuration; longest horizons first (LPT)
   struct Key {
-    int obj, bf16, block, fused;
+    int obj, bf16, block, gen;
     bool operator<(const Key& o) const {
       return obj != o.obj ? obj < o.obj : bf16 != o.bf16 ? bf16 < o.bf16 : block != o.block ? block < o.block
-                                                                                           : fused < o.fused;
+                                                                                           : gen < o.gen;
     }
   };
   std::vector<std::pair<Key, std::vector<Tile>>> rg;
@@ -879,7 +884,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
     const SolveDesc& d = hs[i]->hd;
-    Key k{d.objective, d.noise_bf16, d.block, d.noise_fused};
+    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen};
     Key kn{0, d.noise_bf16, d.block, 0};
     auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
       for (size_t j = 0; j < v.size(); ++j)
@@ -890,7 +895,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     int gi = find(rg, k);
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
     rsmem[gi] = std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, d.block, merge_cap(d.n_tiles)));
-    const int gn = d.noise_fused ? -1 : find(ng, kn);
+    const int gn = d.noise_gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
       rg[gi].second.push_back(Tile{i, t * d.block});
       if (gn >= 0) ng[gn].second.push_back(Tile{i, t * d.block});
@@ -925,7 +930,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
     const Key& k = rg[gi].first;
-    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.fused, rsmem[gi], (int)v.size(), tp, tp});
+    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.gen, rsmem[gi], (int)v.size(), tp, tp});
     tp += v.size();
   }
   for (auto& g : ng) {
@@ -949,7 +954,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->kernels_per_solve = (int)b->noise_groups.size() + (int)b->rollout_groups.size() + (b->n_which > 0 ? 1 : 0);
   if (b->use_graph && b->branches && b->rollout_groups.size() > 1 && b->rollout_groups.size() <= 8) {
     b->kernels_per_solve = b->n_which > 0 ? 1 : 0;
-    for (const auto& g : b->rollout_groups) b->kernels_per_solve += g.fused ? 1 : 2;
+    for (const auto& g : b->rollout_groups) b->kernels_per_solve += g.gen == MPPI_NOISEGEN_KERNEL ? 2 : 1;
   }
   int rc = hostio_alloc(b->io, n);
   if (rc) return cleanup(rc);
@@ -1071,7 +1076,7 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
     for (int obj = 0; obj < 3; ++obj) {
       for (const auto& g : b->rollout_groups)
         if (g.objective == obj &&
-            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.fused) !=
+            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen) !=
                 cudaSuccess)
           status = MPPI_ERR_CUDA;
       cudaEventRecord(ev[2 + obj], s);

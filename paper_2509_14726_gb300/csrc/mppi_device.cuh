@@ -94,7 +94,7 @@ struct SolveDesc {
   float* xref;          // [N+1][13] tracking window used (diagnostics)
   int32_t n_tiles, block;
   int32_t ext_noise;    // 1: use the caller's noise for this solve
-  int32_t noise_fused;  // 1: the rollout draws the normals itself
+  int32_t noise_gen;    // MPPI_NOISEGEN_*: where the normals are drawn
 };
 
 // device-side per-launch inputs and outputs (indexed by the solve's position

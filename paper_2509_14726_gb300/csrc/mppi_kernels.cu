@@ -225,9 +225,10 @@ __device__ __forceinline__ void load_noise(const SolveDesc& d, size_t idx, float
 }
 
 // Generates the standard normals of (sample m, step k) with the noise
-// kernel's Philox / Box-Muller arithmetic, stores them (float32 or bfloat16)
-// for the epilogue and diagnostics, and returns the stored values.
-template <int BF16>
+// kernel's Philox / Box-Muller arithmetic and returns them.  STORE: also
+// writes them (float32 or bfloat16, the values returned) for the epilogue and
+// the diagnostics; without STORE the epilogue draws them again.
+template <int BF16, bool STORE = true>
 __device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int m, int k, float z[kNU], bool five) {
   const size_t idx = (size_t)k * d.K + m;
   float4 v = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
@@ -238,18 +239,20 @@ __device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int
   }
   if (BF16) {
     __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-    uint2 w;
-    w.x = *reinterpret_cast<uint32_t*>(&a);
-    w.y = *reinterpret_cast<uint32_t*>(&b);
-    d.Zb[idx] = w;
+    if (STORE) {
+      uint2 w;
+      w.x = *reinterpret_cast<uint32_t*>(&a);
+      w.y = *reinterpret_cast<uint32_t*>(&b);
+      d.Zb[idx] = w;
+    }
     const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     v = make_float4(fa.x, fa.y, fb.x, fb.y);
     if (five) {
       const __nv_bfloat16 h = __float2bfloat16_rn(z5);
-      d.Z5b[idx] = h;
+      if (STORE) d.Z5b[idx] = h;
       z5 = __bfloat162float(h);
     }
-  } else {
+  } else if (STORE) {
     d.Z4[idx] = v;
     if (five) d.Z5[idx] = z5;
   }
@@ -386,6 +389,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     if (bytes_path) bulk_g2s(sPath, d.path, bytes_path, &mbar);
   }
   DevState* st = d.st;
+  // GEN != 0: the normals are drawn here (GEN 1 stores them, GEN 2 draws them
+  // again in the epilogue) instead of being loaded from the noise kernel's output
+  const uint32_t iter = GEN ? st->iter : 0u;
   // gate frames (computed here from the raw table: centre, yaw, half sizes)
   if (OBJ == MPPI_OBJ_GATE) {
     for (int i = tid; i < d.n_gates; i += blockDim.x) {
@@ -547,11 +553,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
     // software pipeline: the next step's noise is in flight during this step
     float z[kNU], zn[kNU];
-    // GEN: the normals are generated here (one step ahead) instead of being
-    // loaded from the noise kernel's output
-    const uint32_t iter = GEN ? st->iter : 0u;
     if (GEN)
-      gen_noise<BF16>(d, iter, m, 0, zn, five);
+      gen_noise<BF16, GEN == 1>(d, iter, m, 0, zn, five);
     else
       load_noise<BF16>(d, (size_t)m, zn, five);
 #pragma unroll kRolloutUnroll
@@ -560,7 +563,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       for (int j = 0; j < kNU; ++j) z[j] = zn[j];
       if (k + 1 < N) {
         if (GEN)
-          gen_noise<BF16>(d, iter, m, k + 1, zn, five);
+          gen_noise<BF16, GEN == 1>(d, iter, m, k + 1, zn, five);
         else
           load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
       }
@@ -701,7 +704,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     d.J[m] = Jd;
     d.info[m] = passed | ((first + 1) << 16);
   }
-  // (with GEN the epilogue reads noise other threads of this block stored;
+  // (with GEN 1 the epilogue reads noise other threads of this block stored;
   // the barriers inside block_min_d make those stores visible)
   const double m_t = block_min_d(valid ? Jd : INFINITY, red);
   float e = 0.f;
@@ -724,7 +727,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     for (int i = lane; i < nvalid; i += 32) {
       const float w = sE[i];
       float zz[kNU];
-      load_noise<BF16, !GEN>(d, (size_t)k * K + tile.m0 + i, zz, five);
+      if (GEN == 2)
+        gen_noise<BF16, false>(d, iter, tile.m0 + i, k, zz, five);
+      else
+        load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + i, zz, five);
 #pragma unroll
       for (int j = 0; j < kNU; ++j) {
         if (j >= nu) break;
@@ -1022,8 +1028,14 @@ template <int OBJ, int BF16>
 static cudaError_t configure_t() {
   cudaError_t e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  // drawing the noise again in the epilogue stores nothing, so it has no
+  // bfloat16 form
+  if constexpr (!BF16)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(rollout_kernel<OBJ, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return e;
 }
 
 cudaError_t configure_kernels() {
@@ -1040,10 +1052,14 @@ template <int OBJ, int BF16>
 static cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
                                     uint32_t smem, LaunchIO io, cudaStream_t s, int gen) {
   (void)cudaGetLastError();
-  if (gen)
+  if (gen == 2) {
+    if constexpr (BF16) return cudaErrorInvalidValue;
+    else rollout_kernel<OBJ, 0, 2><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  } else if (gen == 1) {
     rollout_kernel<OBJ, BF16, 1><<<n_tiles, block, smem, s>>>(descs, tiles, io);
-  else
+  } else {
     rollout_kernel<OBJ, BF16, 0><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  }
   ++g_launches;
   return cudaGetLastError();
 }

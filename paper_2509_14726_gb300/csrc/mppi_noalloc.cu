@@ -60,7 +60,7 @@ struct Layout {
   size_t desc, st, tiles, U, prev, Z, Z5, J, info, pm, pS, pP, ticket, passcnt, xref, total;
 };
 
-Layout layout_for(int K, int N, int block, int five, int bf16) {
+Layout layout_for(int K, int N, int block, int five, int bf16, bool stored) {
   const int T = (K + block - 1) / block;
   int sq = 1;
   while (sq * sq < T) ++sq;
@@ -77,8 +77,8 @@ Layout layout_for(int K, int N, int block, int five, int bf16) {
   L.tiles = take(sizeof(Tile) * T);
   L.U = take(sizeof(float) * (N * kNU + 8));
   L.prev = take(sizeof(int32_t) * (N + 8));
-  L.Z = take((size_t)N * K * (bf16 ? 8 : 16));
-  L.Z5 = take(five ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
+  L.Z = take(stored ? (size_t)N * K * (bf16 ? 8 : 16) : 16);
+  L.Z5 = take(five && stored ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
   L.J = take(sizeof(double) * K);
   L.info = take(sizeof(int32_t) * K);
   L.pm = take(sizeof(double) * (T + Gn + 1));
@@ -133,8 +133,10 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (block < 32 || block > kMaxBlock || block % 32) return fail(MPPI_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
   if (p.K < 1 || p.N < 1 || p.N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K or N out of range");
   if (!(p.dt > 0) || !(p.lambda > 0)) return fail(MPPI_ERR_ARG, "dt and lambda must be positive");
-  if (p.noise_gen != MPPI_NOISEGEN_KERNEL && p.noise_gen != MPPI_NOISEGEN_FUSED)
+  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_REGEN)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
+  if (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32)
+    return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
   if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return fail(MPPI_ERR_ARG, "noise dtype");
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.objective == MPPI_OBJ_GATE && (d_track->n_gates < 1 || !d_track->gates))
@@ -145,7 +147,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
     return fail(MPPI_ERR_ARG, "tracking needs a reference table");
   const int five = p.objective == MPPI_OBJ_CONTOUR;
   const int bf16 = p.noise_dtype == MPPI_NOISE_BF16;
-  const Layout L = layout_for(p.K, p.N, block, five, bf16);
+  const bool stored = p.noise_gen != MPPI_NOISEGEN_REGEN;  // regenerated noise needs no buffer
+  const Layout L = layout_for(p.K, p.N, block, five, bf16, stored);
   if (L.total > kScratchBytes) {
     char buf[200];
     snprintf(buf, sizeof buf, "K=%d, N=%d need %zu bytes of scratch, more than the %zu-byte static maximum", p.K,
@@ -190,7 +193,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.seed = p.seed;
   d.drone_id = p.drone_id;
   d.noise_bf16 = bf16;
-  d.noise_fused = p.noise_gen == MPPI_NOISEGEN_FUSED;
+  d.noise_gen = p.noise_gen;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -226,10 +229,10 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.U = reinterpret_cast<float*>(b + L.U);
   d.prevcnt = reinterpret_cast<int32_t*>(b + L.prev);
   d.N_cap = p.N;
-  d.Z4 = bf16 ? nullptr : reinterpret_cast<float4*>(b + L.Z);
-  d.Zb = bf16 ? reinterpret_cast<uint2*>(b + L.Z) : nullptr;
-  d.Z5 = (five && !bf16) ? reinterpret_cast<float*>(b + L.Z5) : nullptr;
-  d.Z5b = (five && bf16) ? reinterpret_cast<__nv_bfloat16*>(b + L.Z5) : nullptr;
+  d.Z4 = (stored && !bf16) ? reinterpret_cast<float4*>(b + L.Z) : nullptr;
+  d.Zb = (stored && bf16) ? reinterpret_cast<uint2*>(b + L.Z) : nullptr;
+  d.Z5 = (stored && five && !bf16) ? reinterpret_cast<float*>(b + L.Z5) : nullptr;
+  d.Z5b = (stored && five && bf16) ? reinterpret_cast<__nv_bfloat16*>(b + L.Z5) : nullptr;
   d.J = reinterpret_cast<double*>(b + L.J);
   d.info = reinterpret_cast<int32_t*>(b + L.info);
   d.part_m = reinterpret_cast<double*>(b + L.pm);
@@ -253,7 +256,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, block);
   add_launches(2);
   if (cudaGetLastError() != cudaSuccess) return fail(MPPI_ERR_CUDA, "set-up kernel launch failed");
-  if (!d.noise_fused && launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s) != cudaSuccess)
+  if (d.noise_gen == MPPI_NOISEGEN_KERNEL && launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "noise kernel launch failed");
   LaunchIO io;
   memset(&io, 0, sizeof io);
@@ -263,7 +266,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.u0 = d_u0;
   io.status = nullptr;
   const uint32_t smem = rollout_smem_bytes(p.N, p.objective, d.S, block, d.n_tiles > 32 ? d.n_tiles : 32);
-  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_fused) != cudaSuccess)
+  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");
   return MPPI_OK;
 }

@@ -125,7 +125,7 @@ struct Scratch {
   size_t Z, Z5, J, info, pm, pS, pP, total;
 };
 
-Scratch scratch_for(int K, int N, int block, int five, int bf16) {
+Scratch scratch_for(int K, int N, int block, int five, int bf16, int gen) {
   const int T = (K + block - 1) / block;
   int sq = 1;
   while (sq * sq < T) ++sq;
@@ -137,8 +137,9 @@ Scratch scratch_for(int K, int N, int block, int five, int bf16) {
     o = al256(o + b);
     return r;
   };
-  s.Z = take((size_t)N * K * (bf16 ? 8 : 16));
-  s.Z5 = take(five ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
+  const bool stored = gen != MPPI_NOISEGEN_REGEN;  // regenerated noise needs no buffer
+  s.Z = take(stored ? (size_t)N * K * (bf16 ? 8 : 16) : 16);
+  s.Z5 = take(five && stored ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
   s.J = take(sizeof(double) * K);
   s.info = take(sizeof(int32_t) * K);
   s.pm = take(sizeof(double) * (T + Gn + 1));
@@ -301,6 +302,11 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
     return sfail(MPPI_ERR_ARG, "bad K / N caps");
   if ((K_cap + block - 1) / block > s->max_tiles) return sfail(MPPI_ERR_ARG, "K_cap too large for this server");
   if (p.objective < 0 || p.objective > 2) return sfail(MPPI_ERR_ARG, "unknown objective");
+  if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return sfail(MPPI_ERR_ARG, "noise dtype");
+  if (p.accum < 0 || p.accum > 2) return sfail(MPPI_ERR_ARG, "unknown accumulation mode");
+  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_REGEN ||
+      (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32))
+    return sfail(MPPI_ERR_ARG, "bad noise generation mode");
   if (track->n_gates < 0 || track->n_gates > MPPI_MAX_GATES) return sfail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.objective == MPPI_OBJ_GATE && (track->n_gates < 1 || !track->gates)) return sfail(MPPI_ERR_ARG, "no gates");
   if (p.objective == MPPI_OBJ_CONTOUR && (track->S < 2 || !track->path || !(track->L > 0)))
@@ -392,7 +398,7 @@ int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const fl
     const Drone& d = s->drones[drones[i]];
     if (Ks[i] < 1 || Ks[i] > d.K_cap || Ns[i] < 1 || Ns[i] > d.N_cap)
       return sfail(MPPI_ERR_NOT_ADMITTED, "request K=%d N=%d outside drone %d caps", Ks[i], Ns[i], drones[i]);
-    const Scratch sc = scratch_for(Ks[i], Ns[i], d.block, d.nu == 5, d.hd.noise_bf16);
+    const Scratch sc = scratch_for(Ks[i], Ns[i], d.block, d.nu == 5, d.hd.noise_bf16, d.hd.noise_gen);
     if (sc.total > s->pool.size())
       return sfail(MPPI_ERR_NOT_ADMITTED, "request needs %zu scratch bytes, the pool has %zu", sc.total, s->pool.size());
   }
@@ -442,7 +448,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
       keep.push_back(r);
       continue;
     }
-    const Scratch sc = scratch_for(r.K, r.N, d.block, d.nu == 5, d.hd.noise_bf16);
+    const Scratch sc = scratch_for(r.K, r.N, d.block, d.nu == 5, d.hd.noise_bf16, d.hd.noise_gen);
     size_t off = 0;
     if (!s->pool.alloc(sc.total, &off)) {
       blocked = true;  // the head waits for memory; later arrivals do not jump it
@@ -486,14 +492,15 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     const Drone& d = s->drones[r.drone];
     SolveDesc dd = d.hd;
     char* b = s->pool_base + r.off;
-    const Scratch sc = scratch_for(r.K, r.N, d.block, d.nu == 5, dd.noise_bf16);
+    const Scratch sc = scratch_for(r.K, r.N, d.block, d.nu == 5, dd.noise_bf16, dd.noise_gen);
     dd.K = r.K;
     dd.N = r.N;
     dd.n_tiles = (r.K + d.block - 1) / d.block;
-    dd.Z4 = dd.noise_bf16 ? nullptr : reinterpret_cast<float4*>(b + sc.Z);
-    dd.Zb = dd.noise_bf16 ? reinterpret_cast<uint2*>(b + sc.Z) : nullptr;
-    dd.Z5 = (d.nu == 5 && !dd.noise_bf16) ? reinterpret_cast<float*>(b + sc.Z5) : nullptr;
-    dd.Z5b = (d.nu == 5 && dd.noise_bf16) ? reinterpret_cast<__nv_bfloat16*>(b + sc.Z5) : nullptr;
+    const bool stored = dd.noise_gen != MPPI_NOISEGEN_REGEN;
+    dd.Z4 = (stored && !dd.noise_bf16) ? reinterpret_cast<float4*>(b + sc.Z) : nullptr;
+    dd.Zb = (stored && dd.noise_bf16) ? reinterpret_cast<uint2*>(b + sc.Z) : nullptr;
+    dd.Z5 = (stored && d.nu == 5 && !dd.noise_bf16) ? reinterpret_cast<float*>(b + sc.Z5) : nullptr;
+    dd.Z5b = (stored && d.nu == 5 && dd.noise_bf16) ? reinterpret_cast<__nv_bfloat16*>(b + sc.Z5) : nullptr;
     dd.J = reinterpret_cast<double*>(b + sc.J);
     dd.info = reinterpret_cast<int32_t*>(b + sc.info);
     dd.part_m = reinterpret_cast<double*>(b + sc.pm);
@@ -508,7 +515,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   // tiles: rollout groups by (objective, noise type, block), longest
   // horizons first; the noise launches reuse the same tiles per (type, block)
   struct Group {
-    int obj, bf16, block, fused;
+    int obj, bf16, block, gen;
     std::vector<Tile> t;
     uint32_t smem = 0;
   };
@@ -522,10 +529,10 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     int g = -1;
     for (size_t q = 0; q < groups.size(); ++q)
       if (groups[q].obj == dd.objective && groups[q].bf16 == dd.noise_bf16 && groups[q].block == dd.block &&
-          groups[q].fused == dd.noise_fused)
+          groups[q].gen == dd.noise_gen)
         g = (int)q;
     if (g < 0) {
-      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_fused, {}, 0});
+      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, {}, 0});
       g = (int)groups.size() - 1;
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * dd.block});
@@ -554,11 +561,11 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   io.u0 = sl.d_u0;
   io.status = sl.d_status;
   for (size_t q = 0; q < groups.size(); ++q)
-    if (!groups[q].fused)
+    if (groups[q].gen == MPPI_NOISEGEN_KERNEL)
       SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm));
   for (size_t q = 0; q < groups.size(); ++q)
     SCU(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
-                       groups[q].block, groups[q].smem, io, stm, groups[q].fused));
+                       groups[q].block, groups[q].smem, io, stm, groups[q].gen));
   SCU(launch_nominal(ddesc, reinterpret_cast<const int32_t*>(sl.dev + st.which), (int)which.size(), stm));
   SCU(cudaEventRecord(sl.done, stm));
   sl.reqs.swap(batch);

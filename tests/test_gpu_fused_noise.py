@@ -1,9 +1,10 @@
-"""Noise drawn inside the rollout (MPPI_NOISEGEN_FUSED) against the separate
-Philox pass and against the FP64 oracle.
+"""Noise drawn inside the rollout -- stored (MPPI_NOISEGEN_FUSED) or drawn
+again by the update and never stored (MPPI_NOISEGEN_REGEN) -- against the
+separate Philox pass and against the FP64 oracle.
 
-The fused rollout evaluates the same Philox4x32-10 / Box-Muller arithmetic on
-the same counters (Sec. III-B, Eq. 3), so the stored noise is bit-identical
-to the two-kernel path's.  The rest of the rollout is a separate compilation
+Both evaluate the same Philox4x32-10 / Box-Muller arithmetic on the same
+counters (Sec. III-B, Eq. 3), so the fused path's stored noise is
+bit-identical to the two-kernel path's.  The rest of the rollout is a separate compilation
 whose floating-point contractions the compiler chooses on its own, so costs
 and the update agree to binary32 rounding (observed: 1e-8 relative in J),
 not bit for bit; the same mode is bit-exact between the single, batched and
@@ -63,13 +64,16 @@ def _same(a, b):
     np.testing.assert_array_equal(a.costs(), b.costs())
     np.testing.assert_array_equal(a.unew(), b.unew())
     np.testing.assert_array_equal(a.nominal(), b.nominal())
-    np.testing.assert_array_equal(a.noise(), b.noise())
+    if a.params.noise_gen != 2:
+        np.testing.assert_array_equal(a.noise(), b.noise())
     assert a.export_state() == b.export_state()
 
 
 def _close(a, b):
-    """Same noise bit for bit; costs and update to binary32 rounding."""
-    np.testing.assert_array_equal(a.noise(), b.noise())
+    """Same noise bit for bit (where a stores it); costs and update to
+    binary32 rounding."""
+    if a.params.noise_gen != 2:
+        np.testing.assert_array_equal(a.noise(), b.noise())
     na, fa = a.sample_info()
     nb, fb = b.sample_info()
     same = (na == nb) & (fa == fb)
@@ -81,13 +85,16 @@ def _close(a, b):
     assert np.abs(a.nominal() - b.nominal()).max() <= U_ABS_TOL
 
 
+GEN_CASES = [(1, 0), (1, 1), (2, 0)]  # (noise generation, bf16 storage)
+
+
 @pytest.mark.parametrize("objective", [0, 1, 2])
-@pytest.mark.parametrize("bf16", [0, 1])
+@pytest.mark.parametrize("gen,bf16", GEN_CASES)
 @pytest.mark.parametrize("K,N,block", [(1000, 13, 128), (3001, 20, 64), (33, 3, 32)])
-def test_fused_matches_separate(O, M, objective, bf16, K, N, block):
+def test_drawn_in_rollout_matches_separate(O, M, objective, gen, bf16, K, N, block):
     case = _case(objective, K, N)
     kw = dict(noise_dtype=bf16, block=block)
-    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_FUSED, **kw)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=gen, **kw)
     b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL, **kw)
     t0 = 0.37
     x0 = _x0(O, case, t0)
@@ -102,14 +109,18 @@ def test_fused_matches_separate(O, M, objective, bf16, K, N, block):
 
 
 @pytest.mark.parametrize("objective", [0, 1, 2])
-def test_fused_against_oracle(O, M, objective):
+@pytest.mark.parametrize("gen", [1, 2])
+def test_drawn_in_rollout_against_oracle(O, M, objective, gen):
     case = _case(objective, 4096, 50)
-    gpu, ora = make_pair(case, noise_gen=M.NOISEGEN_FUSED)
+    gpu, ora = make_pair(case, noise_gen=gen)
     t0 = 0.37
     x0 = _x0(O, case, t0)
     gpu.solve(x0, t0)
     r = ora.solve(x0, t0)
-    compare(gpu, r, f"fused noise, objective {objective}")
+    compare(gpu, r, f"noise generation {gen}, objective {objective}")
+    if gen == 2:
+        gpu.close()
+        return
     # the stored normals are the oracle's Philox / Box-Muller draws
     Zg = gpu.noise()
     ms = range(0, case.sc.K, 257)
@@ -120,14 +131,14 @@ def test_fused_against_oracle(O, M, objective):
 
 @pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_batch_with_mixed_noise_modes(M, use_graph):
-    """A plan holding fused and separate-noise handles of every objective
+    """A plan holding handles of every noise generation mode and objective
     gives each solve exactly what it gets alone in the same mode."""
     items = W.c3_batch(n_drones=8, K_lo=300, K_hi=3000, N_lo=5, N_hi=40)
     trip = []
     for i, it in enumerate(items):
         sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id)
         case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
-        mode = M.NOISEGEN_FUSED if i % 2 == 0 else M.NOISEGEN_KERNEL
+        mode = i % 3  # separate pass, fused, regenerated
         g1 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         g2 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         trip.append((g1, g2, case))
@@ -152,7 +163,7 @@ def test_server_with_fused_noise(M):
     alone = []
     for i, d in enumerate(fleet):
         sc = W.SolveConfig(objective=d.objective, K=1024, N=30, dt=0.02, drone_id=d.drone_id)
-        mode = M.NOISEGEN_FUSED if i % 3 else M.NOISEGEN_KERNEL
+        mode = i % 3
         srv.add_drone(W.ModelConfig(), sc, d.track, 2048, 30, noise_gen=mode)
         alone.append(M.Controller(W.ModelConfig(), sc, d.track, K_cap=2048, N_cap=30, noise_gen=mode))
     X0 = np.array([d.x0 for d in fleet])
@@ -197,5 +208,27 @@ def test_caller_noise_on_a_fused_handle(M):
         else:
             assert np.abs(ua - ub).max() <= U_ABS_TOL
             _close(a, b)
+    a.close()
+    b.close()
+
+
+def test_regenerated_noise_has_no_buffer(M):
+    """REGEN stores no noise: the handle is smaller by the noise buffer, the
+    noise getters refuse, and bfloat16 storage is refused at creation."""
+    case = _case(1, 4096, 50)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_REGEN)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL)
+    saved = M.mppi_device_bytes(b.h) - M.mppi_device_bytes(a.h)
+    # 16 B + the 5th plane's 4 B per rollout step, less two 256-B placeholders
+    assert saved >= 4096 * 50 * 20 - 512
+    with pytest.raises(M.MppiError) as e:
+        a.noise()
+    assert e.value.code == M.MPPI_ERR_ARG
+    z = torch.zeros((50, 4096, 4), device="cuda")
+    with pytest.raises(M.MppiError):
+        M.mppi_set_noise(a.h, z.data_ptr(), z.data_ptr())
+    with pytest.raises(M.MppiError) as e:
+        M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_REGEN, noise_dtype=M.NOISE_BF16)
+    assert e.value.code == M.MPPI_ERR_ARG
     a.close()
     b.close()
