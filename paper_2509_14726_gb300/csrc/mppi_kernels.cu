@@ -107,6 +107,55 @@ __device__ double block_sum_d(double v, double* red) {
   return r;
 }
 
+// Binary32 forms of the block reductions.  On this GPU a dependent FP64
+// operation costs about ten times the latency of an FP32 one, and these
+// reductions sit on every block's critical path, so the default accumulation
+// modes keep the tile minimum in binary32 and the sums as compensated
+// (hi, lo) binary32 pairs; the MPPI_ACC_F64 mode keeps FP64 throughout.
+// (h, l) += (h2, l2) with TwoSum, renormalised
+__device__ __forceinline__ void add2(float& h, float& l, float h2, float l2) {
+  float s, e;
+  two_sum(h, h2, s, e);
+  const float t = e + l + l2;
+  two_sum(s, t, h, l);
+}
+__device__ __forceinline__ void warp_sum2_f(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    add2(h, l, h2, l2);
+  }
+}
+__device__ float block_min_f(float v, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_min_f(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float r = INFINITY;
+  for (int i = 0; i < nw; ++i) r = fminf(r, red[i]);
+  return r;
+}
+// block total of (h, l) pairs in a fixed order (deterministic); red holds >= 64 floats
+__device__ void block_sum2_f(float& h, float& l, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  warp_sum2_f(h, l);
+  __syncthreads();
+  if (lane == 0) {
+    red[2 * wid] = h;
+    red[2 * wid + 1] = l;
+  }
+  __syncthreads();
+  h = red[0];
+  l = red[1];
+  for (int i = 1; i < nw; ++i) add2(h, l, red[2 * i], red[2 * i + 1]);
+}
+__device__ __forceinline__ double pack2(float h, float l) {
+  float2 r = make_float2(h, l);
+  return *reinterpret_cast<double*>(&r);
+}
+__device__ __forceinline__ float2 unpack2(double raw) { return *reinterpret_cast<const float2*>(&raw); }
+
 // ---------------------------------------------------------------------------
 // gate geometry (Sec. IV-A): s = n . (p - c); a pass goes from s < 0 to s >= 0
 // through the opening (lateral |l . e| <= half_w, vertical |e_z| <= half_h)
@@ -262,7 +311,8 @@ __device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int
 // ---------------------------------------------------------------------------
 // flash-softmax merge of partials (Eq. 4 / Eq. 5 in split form):
 //   m = min m_i, s_i = exp(-(m_i - m) / lambda), S = sum S_i s_i,
-//   P = sum P_i s_i  (P in float hi/lo pairs, compensated products)
+//   P = sum P_i s_i.  Binary32 minimum and scales with S and P as
+//   compensated (hi, lo) pairs, or FP64 throughout (MPPI_ACC_F64).
 // ---------------------------------------------------------------------------
 struct MergeIn {
   const double* m;   // [n]
@@ -272,6 +322,44 @@ struct MergeIn {
 
 __device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int NNU, double* out_m, double* out_S,
                                double* out_P, double* scale_s, double* red, int f64) {
+  if (!f64) {
+    // binary32 minimum and scales; S and P as compensated (hi, lo) pairs
+    float* redf = reinterpret_cast<float*>(red);
+    float* scale_f = reinterpret_cast<float*>(scale_s);
+    float mloc = INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mloc = fminf(mloc, (float)__ldcg(in.m + i));
+    const float mm = block_min_f(mloc, redf);
+    float sh = 0.f, sl = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float mi = (float)__ldcg(in.m + i);
+      const float sc = (isinf(mm) || isinf(mi)) ? 0.f : expf(-(mi - mm) * d.inv_lambda);
+      scale_f[i] = sc;
+      const float2 Si = unpack2(__ldcg(in.S + i));
+      const float p = Si.x * sc;
+      add2(sh, sl, p, fmaf(Si.x, sc, -p) + Si.y * sc);
+    }
+    block_sum2_f(sh, sl, redf);  // its barriers make scale_f visible
+    for (int o = threadIdx.x; o < NNU; o += blockDim.x) {
+      float hi = 0.f, lo = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const float2 v = unpack2(__ldcg(in.P + (size_t)i * NNU + o));
+        const float sc = scale_f[i];
+        const float p = v.x * sc;
+        float t, e;
+        two_sum(hi, p, t, e);
+        hi = t;
+        lo += e + fmaf(v.x, sc, -p) + v.y * sc;
+      }
+      float t, e;
+      two_sum(hi, lo, t, e);
+      out_P[o] = pack2(t, e);
+    }
+    if (threadIdx.x == 0) {
+      *out_m = (double)mm;
+      *out_S = pack2(sh, sl);
+    }
+    return;
+  }
   double mloc = INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x) mloc = fmin(mloc, __ldcg(in.m + i));
   const double mm = block_min_d(mloc, red);
@@ -312,12 +400,6 @@ __device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int 
     *out_m = mm;
     *out_S = SS;
   }
-}
-
-__device__ __forceinline__ double part_value(double raw, int f64) {
-  if (f64) return raw;
-  const float2 v = *reinterpret_cast<const float2*>(&raw);
-  return (double)v.x + (double)v.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -699,25 +781,40 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
 
   // ---- per-sample outputs and the block's share of Eq. 4 ----
   const double Jd = (double)Jh - (double)Jc;
-  const bool valid = active && isfinite(Jd);
+  const float Jf = Jh - Jc;
+  const bool valid = active && isfinite(Jh) && isfinite(Jc) && isfinite(Jf);
   if (active) {
     d.J[m] = Jd;
     d.info[m] = passed | ((first + 1) << 16);
   }
+  const int acc = d.accum;
   // (with GEN 1 the epilogue reads noise other threads of this block stored;
-  // the barriers inside block_min_d make those stores visible)
-  const double m_t = block_min_d(valid ? Jd : INFINITY, red);
+  // the barriers inside the block reductions make those stores visible)
+  double m_t, S_t;  // tile minimum and sum of exp weights (packed (hi, lo) unless FP64)
   float e = 0.f;
-  if (valid && !isinf(m_t)) e = expf(-(float)(Jd - m_t) * d.inv_lambda);
-  if (tid < B) sE[tid] = e;
-  const double S_t = block_sum_d((double)e, red);  // also publishes sE
+  if (acc == MPPI_ACC_F64) {
+    m_t = block_min_d(valid ? Jd : INFINITY, red);
+    if (valid && !isinf(m_t)) e = expf(-(float)(Jd - m_t) * d.inv_lambda);
+    if (tid < B) sE[tid] = e;
+    S_t = block_sum_d((double)e, red);  // also publishes sE
+  } else {
+    // any common shift leaves Eq. 4 unchanged: the binary32 minimum of the
+    // rounded costs serves; J - m_t is formed from the compensated pair
+    float* redf = reinterpret_cast<float*>(red);
+    const float mf = block_min_f(valid ? Jf : INFINITY, redf);
+    if (valid && !isinf(mf)) e = expf(-(((Jh - mf) - Jc) * d.inv_lambda));
+    if (tid < B) sE[tid] = e;
+    float sh = e, sl = 0.f;
+    block_sum2_f(sh, sl, redf);  // also publishes sE
+    m_t = (double)mf;
+    S_t = pack2(sh, sl);
+  }
 
   // ---- weighted deviation sums per (step, input) of this tile (Eq. 5) ----
   const int nvalid = min(B, K - tile.m0);
   const int NNU = N * kNU;
   const int tile_in_solve = tile.m0 / B;
   double* myP = d.part_P + (size_t)tile_in_solve * NNU;
-  const int acc = d.accum;
   for (int k = wid; k < N; k += nw) {
     const float* Uk = sU + kNU * k;
     float hi[kNU], lo[kNU];
@@ -839,12 +936,25 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     merge_partials(d, in, n, NNU, &s_m, &s_S, fP, sMerge, red, f64);
     __threadfence_block();
     __syncthreads();
-    const bool degenerate = isinf(s_m) || !(s_S > 0.0);
+    const float2 S2 = unpack2(s_S);
+    const double S_total = f64 ? s_S : (double)S2.x + (double)S2.y;
+    const bool degenerate = isinf(s_m) || !(S_total > 0.0);
     float* u0o = io.u0 + (size_t)tile.solve * kNU;
     for (int o = tid; o < NNU; o += blockDim.x) {
       const int k = o / kNU, j = o - k * kNU;
       float v = sU[o];
-      if (!degenerate && j < nu) v = (float)((double)sU[o] + part_value(fP[o], f64) / s_S);
+      if (!degenerate && j < nu) {
+        if (f64) {
+          v = (float)((double)sU[o] + fP[o] / s_S);
+        } else {
+          // (P_hi + P_lo) / (S_hi + S_lo) with one correction step
+          const float2 P2 = unpack2(fP[o]);
+          float q = P2.x / S2.x;
+          const float r = (fmaf(-q, S2.x, P2.x) + P2.y) - q * S2.y;
+          q += r / S2.x;
+          v = sU[o] + q;
+        }
+      }
       if (j >= nu) v = 0.f;
       d.unew[o] = v;
       if (k == 0) u0o[j] = v;
@@ -877,7 +987,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         st->scal[1] = (double)s_vth0;
       }
       st->scal[2] = s_m;
-      st->scal[3] = s_S;
+      st->scal[3] = S_total;
       if (io.status) io.status[tile.solve] = degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
       d.ticket[0] = 0u;
     }

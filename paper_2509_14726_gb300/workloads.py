@@ -401,6 +401,16 @@ def c2_full_scale(objective: int = OBJ_GATE, seed: int = 7):
     return ModelConfig(), cfg, tr, hover_state_before_gate(tr.gates, 0, 1.0)
 
 
+def paper_table1(objective: int = OBJ_GATE, K: int = 8192, seed: int = 7):
+    """The solve size of the paper's simulation parameters (Table I): 8192
+    samples, horizon 20, dt 0.03 s, temperature 0.01, on the seeded 7-gate
+    course (the paper's tracks are not available).  K=2048 is the sample count
+    of its onboard flights at 50 Hz (Sec. V-C)."""
+    tr = random_course(seed, 7)
+    cfg = SolveConfig(objective=objective, K=K, N=20, dt=0.03, lam=0.01, seed=0)
+    return ModelConfig(), cfg, tr, hover_state_before_gate(tr.gates, 0, 1.0)
+
+
 @dataclasses.dataclass
 class BatchItem:
     drone_id: int
