@@ -31,7 +31,11 @@
  *     (0, 1]; Box-Muller turns (x0, x1) and (x2, x3) into four normals
  *   - inputs are clamped to their box; the clamped samples are rolled out and
  *     averaged; the feasibility penalty acts on body rate and altitude
- *   - warm start shifts the new nominal by one step and repeats the last row.
+ *   - warm start shifts the new nominal by one step and repeats the last row
+ *     (warm_start 0); warm_start 1 keeps the complete sequence, the literal
+ *     reading of Sec. III-B;
+ *   - nominal_sample 1 makes candidate 0 the unperturbed nominal (Eq. 3 with
+ *     du = 0), a common MPPI variant the paper does not use.
  *
  * Parity status: every function here is pinned by a CPU test against a
  * closed form, an invariant, a brute-force search or an independent library
@@ -78,6 +82,12 @@ typedef struct {
   double Q[13], QN[13], R[4];
   /* near-plane / near-edge reporting band, metres */
   double flag_eps;
+  /* variants of the sampling and the warm start (Sec. III-B):
+   * nominal_sample 1: sample 0 carries no perturbation (U^0 = U*, clamped);
+   * warm_start 0: shift the new nominal by one step and repeat the last row,
+   *            1: keep the complete new sequence as the next nominal */
+  int32_t nominal_sample;
+  int32_t warm_start;
 } or_params;
 
 typedef struct {
@@ -546,7 +556,9 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
   for (int32_t m = 0; m < K; ++m) {
     for (int32_t k = 0; k < N; ++k) {
       double z[5] = {0, 0, 0, 0, 0};
-      if (out && out->Z_in) {
+      if (pr->nominal_sample && m == 0) {
+        /* the unperturbed nominal is one of the candidates */
+      } else if (out && out->Z_in) {
         for (int j = 0; j < OR_NU; ++j) z[j] = out->Z_in[((size_t)k * K + m) * OR_NU + j];
       } else {
         double z4[4];
@@ -625,9 +637,10 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
   if (out && out->passcnt) memcpy(out->passcnt, pc, sizeof(int32_t) * (N + 1));
   if (out && out->Xnom) memcpy(out->Xnom, Xn, sizeof(double) * 13 * (N + 1));
 
-  /* warm start: shift by one step, repeat the last row (Sec. III-B) */
+  /* warm start (Sec. III-B): shift by one step and repeat the last row, or
+   * keep the complete sequence */
   for (int32_t k = 0; k < N; ++k) {
-    int32_t src = k + 1 < N ? k + 1 : N - 1;
+    int32_t src = pr->warm_start == 1 ? k : (k + 1 < N ? k + 1 : N - 1);
     for (int j = 0; j < OR_NU; ++j) st->U[OR_NU * k + j] = Unew[OR_NU * src + j];
   }
   st->n_nom = N;

@@ -35,7 +35,8 @@ class OrParams(C.Structure):
                 ("seed", U32), ("drone_id", U32), ("w_limit", D), ("q_near", D), ("r_near", D),
                 ("temporal_rule", I32), ("q_lag", D), ("q_cont", D), ("q_omega", D * 3), ("r_dv", D),
                 ("r_dthrust", D), ("mu", D), ("v_theta_max", D), ("theta_back", D), ("theta_ahead", D),
-                ("Q", D * 13), ("QN", D * 13), ("R", D * 4), ("flag_eps", D)]
+                ("Q", D * 13), ("QN", D * 13), ("R", D * 4), ("flag_eps", D), ("nominal_sample", I32),
+                ("warm_start", I32)]
 
 
 class OrTrack(C.Structure):
@@ -141,6 +142,8 @@ def make_params(sc) -> OrParams:
     p.QN[:] = list(sc.QN)
     p.R[:] = list(sc.R)
     p.flag_eps = sc.flag_eps
+    p.nominal_sample = getattr(sc, "nominal_sample", 0)
+    p.warm_start = getattr(sc, "warm_start", 0)
     return p
 
 

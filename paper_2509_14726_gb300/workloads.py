@@ -91,6 +91,8 @@ class SolveConfig:
     QN: Tuple[float, ...] = (20.0,) * 3 + (0.2,) * 3 + (2.0,) * 4 + (0.02,) * 3
     R: Tuple[float, float, float, float] = (0.001, 0.01, 0.01, 0.01)
     flag_eps: float = 1.0e-5
+    nominal_sample: int = 0  # 1: sample 0 is the unperturbed nominal
+    warm_start: int = 0      # 0: shift by one step, 1: keep the complete sequence
 
 
 @dataclasses.dataclass

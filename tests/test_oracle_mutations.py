@@ -46,7 +46,11 @@ MUTATIONS = [
      "w[m] = isfinite(J[m]) ? exp(-(J[m] - Jmin) / pr->lambda) : 0.0;",
      "w[m] = isfinite(J[m]) ? exp(-(J[m] - Jmin) * pr->lambda) : 0.0;"),
     ("warm start without the shift",
-     "int32_t src = k + 1 < N ? k + 1 : N - 1;", "int32_t src = k;"),
+     "(k + 1 < N ? k + 1 : N - 1);", "k;"),
+    ("kept warm start shifted anyway",
+     "pr->warm_start == 1 ? k :", "pr->warm_start == 1 ? (k + 1 < N ? k + 1 : N - 1) :"),
+    ("nominal candidate perturbed like the others",
+     "if (pr->nominal_sample && m == 0) {", "if (pr->nominal_sample && m < 0) {"),
     ("samples not clamped",
      "u[j] = clampd(Unom[OR_NU * k + j] + pr->sigma[j] * z[j], md->u_min[j], md->u_max[j]);",
      "u[j] = Unom[OR_NU * k + j] + pr->sigma[j] * z[j];"),

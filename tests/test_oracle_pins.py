@@ -632,6 +632,48 @@ def test_lambda_to_infinity_gives_the_sample_mean(oracle_mod):
     np.testing.assert_allclose(r["Unew"][:, :4], us[:, :, :4].mean(0), atol=1e-9)
 
 
+def _hover_reference(p=(1.0, 2.0, 3.0), h=0.04):
+    """A tracking reference that hovers at p (two equal rows)."""
+    x = _state(p=p)
+    base = _line_track()
+    return W.Track(base.gates, True, base.path, 100.0, np.vstack([x, x]), h), x
+
+
+def test_nominal_sample_is_the_unperturbed_nominal(oracle_mod):
+    """nominal_sample = 1 makes candidate 0 the nominal itself (no
+    perturbation, Eq. 3 with du = 0).  Hovering on a hover reference, the
+    hover nominal costs 0 (Eq. 8: no state error, u = u_hover) and every
+    perturbed candidate costs more, so as lambda -> 0 the update (Eq. 4, 5)
+    returns the hover sequence exactly; without the nominal candidate it
+    returns a perturbed sample."""
+    mc = _mc()
+    tr, x0 = _hover_reference()
+    sc = W.SolveConfig(objective=2, K=64, N=8, dt=0.04, lam=1e-9, nominal_sample=1)
+    r = oracle_mod.OracleController(mc, sc, tr).solve(x0, 0.0, want_Z=True)
+    assert np.all(r["Z"][:, 0, :] == 0)
+    assert r["J"][0] < 1e-20 and np.all(r["J"][1:] > 1e-6)
+    np.testing.assert_array_equal(r["Unew"][:, 0], np.full(sc.N, mc.hover))
+    np.testing.assert_array_equal(r["Unew"][:, 1:4], 0.0)
+    sc.nominal_sample = 0
+    r0 = oracle_mod.OracleController(mc, sc, tr).solve(x0, 0.0)
+    assert np.max(np.abs(r0["Unew"][:, 1:4])) > 1e-3
+
+
+def test_warm_start_keeps_the_whole_sequence(oracle_mod):
+    """warm_start = 1 (the complete new sequence is the next nominal, no
+    shift): the nominal equals U*_new row for row, and the next solve samples
+    around it -- its update is the weighted mean of clamp(U*_new + sigma z)."""
+    mc, sc, tr, x0 = _small_case()
+    sc.warm_start = 1
+    ctl = oracle_mod.OracleController(mc, sc, tr)
+    r = ctl.solve(x0, 0.0)
+    np.testing.assert_array_equal(ctl.nominal, r["Unew"])
+    r2 = ctl.solve(x0, 0.0, want_Z=True)
+    us = np.clip(r["Unew"][None] + np.asarray(sc.sigma) * r2["Z"].transpose(1, 0, 2), mc.u_min, mc.u_max)
+    us[:, :, 4] = 0
+    np.testing.assert_allclose(r2["Unew"], np.einsum("m,mkj->kj", r2["w"], us), atol=1e-12)
+
+
 def test_noise_stream_and_iteration_counter(oracle_mod):
     mc, sc, tr, x0 = _small_case()
     ctl = oracle_mod.OracleController(mc, sc, tr)
