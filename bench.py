@@ -71,6 +71,45 @@ def measured_traffic(steps_by_objective):
     return sum(per[names[o]] * steps_by_objective[o] for o in (0, 1, 2))
 
 
+def paper_table1_latency(M, W, reps: int = 300) -> dict:
+    """Single-solve latency at the paper's Table I size for each objective
+    (the paper reports about 0.4 ms on an RTX 3090 for 8192 samples)."""
+    import torch
+    out = {}
+    names = {0: "gate", 1: "contour", 2: "track"}
+    for K in (8192, 2048):
+        for obj in (0, 1, 2):
+            mc, sc, tr, x0 = W.paper_table1(obj, K)
+            if obj == 2:
+                x0 = tr.ref[0].astype(np.float64)  # on the reference at t = 0
+            ctl = M.Controller(mc, sc, tr)
+            for _ in range(30):
+                ctl.solve(x0, 0.0)
+            lat = []
+            for _ in range(reps):
+                t = time.perf_counter()
+                ctl.solve(x0, 0.0)
+                lat.append(time.perf_counter() - t)
+            s = torch.cuda.Stream()
+            dx = torch.tensor(np.float32(x0), device="cuda")
+            du = torch.zeros(5, dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(s):
+                for _ in range(10):
+                    M.mppi_solve_async(ctl.h, dx.data_ptr(), 0.0, s, du.data_ptr())
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for _ in range(reps):
+                    M.mppi_solve_async(ctl.h, dx.data_ptr(), 0.0, s, du.data_ptr())
+                e1.record(s)
+            s.synchronize()
+            out[f"K{K}_N20_{names[obj]}"] = {
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "device_ms_per_solve": e0.elapsed_time(e1) / reps}
+            ctl.close()
+    out["paper_rtx3090_ms"] = 0.4
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,6 +439,10 @@ def main():
             "value": 4096 * 50 / float(np.mean(lat2)), "unit": "rollout-steps/s"}
         c2.close()
         e2e["batched_vs_plain_solves_per_s"] = e2e["solves_per_s"] / plain["batch_one_solve_per_launch"]["solves_per_s"]
+        # the paper's solve size (Table I: 8192 samples, horizon 20, dt 0.03,
+        # lambda 0.01; 2048 samples onboard): host-synchronous mppi_solve
+        # latency, and device time per solve back to back
+        plain["paper_table1_single_solve"] = paper_table1_latency(M, W)
 
     # ---- serving: a fleet at its own rates, continuous batching vs plain ----
     serving_out = None

@@ -69,6 +69,10 @@ enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1, MPPI_NOISEGEN_REGEN = 
 /* accumulation of the K-sample weighted update sum (Eq. 5) */
 enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
 enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };
+/* warm start of the next solve (Sec. III-B): shift the new sequence by one
+ * step and repeat its last row, or keep the complete sequence (the literal
+ * reading) */
+enum { MPPI_WARM_SHIFT = 0, MPPI_WARM_KEEP = 1 };
 
 #define MPPI_NX 13
 #define MPPI_NU 5
@@ -120,6 +124,8 @@ typedef struct {
   int32_t N_cap;         /* largest N later solves may use (0 = N) */
   int32_t K_cap;         /* largest K later solves may use (0 = K) */
   int32_t noise_gen;     /* MPPI_NOISEGEN_* */
+  int32_t nominal_sample; /* 1: sample 0 is the unperturbed nominal (Eq. 3 with du = 0) */
+  int32_t warm_start;    /* MPPI_WARM_* */
 } mppi_params_t;
 
 /* Track: waypoints W, arc-length path P_arc and reference tau_ref
@@ -238,7 +244,10 @@ int mppi_set_gate_index(mppi_handle h, int32_t gate);
 /* Uses caller-provided standard normals for the next solve instead of
  * Philox: d_Z is [N][K][4] float32 (or bf16 when the handle stores BF16
  * noise) plus, for contouring, d_Z5 [N][K] of the same type.  Device
- * pointers; the data is copied on `stream` before this returns. */
+ * pointers; the data is copied on `stream` before this returns.  With
+ * nominal_sample set, sample 0's column is zeroed after the copy (it is the
+ * unperturbed nominal).  MPPI_ERR_ARG for a handle with MPPI_NOISEGEN_REGEN
+ * (it has no noise buffer). */
 int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* stream);
 
 /* Philox4x32-10 (Salmon et al., SC'11), run on the device with the same

@@ -133,7 +133,7 @@ struct mppi_batch_s {
   int n = 0;
   SolveDesc* d_descs = nullptr;
   struct Group {
-    int objective, bf16, block, gen;  // gen: MPPI_NOISEGEN_*
+    int objective, bf16, block, gen, nom;  // gen: MPPI_NOISEGEN_*; nom: nominal candidate
     uint32_t smem;
     int n_tiles;
     Tile* d_tiles;
@@ -144,7 +144,7 @@ struct mppi_batch_s {
   cudaEvent_t join[8] = {};
   std::vector<Group> rollout_groups;
   struct NGroup {
-    int bf16, block, n_tiles;
+    int bf16, block, nom, n_tiles;
     Tile* d_tiles;
   };
   std::vector<NGroup> noise_groups;
@@ -188,6 +188,9 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p->noise_gen == MPPI_NOISEGEN_REGEN && p->noise_dtype != MPPI_NOISE_F32)
     return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
+  if (p->nominal_sample != 0 && p->nominal_sample != 1) return fail(MPPI_ERR_ARG, "nominal_sample must be 0 or 1");
+  if (p->warm_start != MPPI_WARM_SHIFT && p->warm_start != MPPI_WARM_KEEP)
+    return fail(MPPI_ERR_ARG, "unknown warm start");
   int blk = p->block ? p->block : 128;
   if (blk < 32 || blk > rollout_max_block() || blk % 32)
     return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
@@ -272,6 +275,8 @@ void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int 
   d.drone_id = p.drone_id;
   d.noise_bf16 = p.noise_dtype == MPPI_NOISE_BF16;
   d.noise_gen = p.noise_gen;
+  d.nominal_sample = p.nominal_sample ? 1 : 0;
+  d.warm_keep = p.warm_start == MPPI_WARM_KEEP ? 1 : 0;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -570,7 +575,7 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   } else if (d.noise_gen != MPPI_NOISEGEN_KERNEL) {
     gen = d.noise_gen;
   } else {
-    CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s));
+    CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
   }
   const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, h->block, merge_cap(d.n_tiles));
   CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen));
@@ -760,9 +765,15 @@ int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* strea
   if (d.noise_gen == MPPI_NOISEGEN_REGEN) return fail(MPPI_ERR_ARG, "a regenerating handle has no noise buffer");
   const size_t nk = (size_t)d.N * d.K;
   const size_t el = d.noise_bf16 ? 2 : 4;
-  CU(cudaMemcpyAsync(d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4, d_Z, nk * 4 * el, cudaMemcpyDeviceToDevice, s));
-  if (h->nu == 5)
-    CU(cudaMemcpyAsync(d.noise_bf16 ? (void*)d.Z5b : (void*)d.Z5, d_Z5, nk * el, cudaMemcpyDeviceToDevice, s));
+  void* z4 = d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4;
+  void* z5 = d.noise_bf16 ? (void*)d.Z5b : (void*)d.Z5;
+  CU(cudaMemcpyAsync(z4, d_Z, nk * 4 * el, cudaMemcpyDeviceToDevice, s));
+  if (h->nu == 5) CU(cudaMemcpyAsync(z5, d_Z5, nk * el, cudaMemcpyDeviceToDevice, s));
+  if (d.nominal_sample) {
+    // the nominal candidate carries no perturbation: zero its column
+    CU(cudaMemset2DAsync(z4, (size_t)d.K * 4 * el, 0, 4 * el, d.N, s));
+    if (h->nu == 5) CU(cudaMemset2DAsync(z5, (size_t)d.K * el, 0, el, d.N, s));
+  }
   h->ext_noise_pending = true;
   return MPPI_OK;
 }
@@ -815,7 +826,8 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     const auto& g = b->rollout_groups[i];
     cudaStream_t bs = b->branch_streams[i];
     CU(cudaStreamWaitEvent(bs, b->fork, 0));
-    if (g.gen == MPPI_NOISEGEN_KERNEL) CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs));
+    if (g.gen == MPPI_NOISEGEN_KERNEL)
+      CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs, g.nom));
     CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen));
     CU(cudaEventRecord(b->join[i], bs));
     CU(cudaStreamWaitEvent(s, b->join[i], 0));
@@ -824,7 +836,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
 }
 
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
-  for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s));
+  for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom));
   for (const auto& g : b->rollout_groups)
     CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen));
   return MPPI_OK;
@@ -864,10 +876,13 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->branches = use_graph == 1;
   // group tiles by launch configuration; longest horizons first (LPT)
   struct Key {
-    int obj, bf16, block, gen;
+    int obj, bf16, block, gen, nom;
     bool operator<(const Key& o) const {
-      return obj != o.obj ? obj < o.obj : bf16 != o.bf16 ? bf16 < o.bf16 : block != o.block ? block < o.block
-                                                                                           : gen < o.gen;
+      if (obj != o.obj) return obj < o.obj;
+      if (bf16 != o.bf16) return bf16 < o.bf16;
+      if (block != o.block) return block < o.block;
+      if (gen != o.gen) return gen < o.gen;
+      return nom < o.nom;
     }
   };
   std::vector<std::pair<Key, std::vector<Tile>>> rg;
@@ -884,8 +899,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
     const SolveDesc& d = hs[i]->hd;
-    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen};
-    Key kn{0, d.noise_bf16, d.block, 0};
+    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen, d.nominal_sample};
+    Key kn{0, d.noise_bf16, d.block, 0, d.nominal_sample};
     auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
       for (size_t j = 0; j < v.size(); ++j)
         if (!(v[j].first < key) && !(key < v[j].first)) return (int)j;
@@ -930,14 +945,14 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
     const Key& k = rg[gi].first;
-    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.gen, rsmem[gi], (int)v.size(), tp, tp});
+    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.gen, k.nom, rsmem[gi], (int)v.size(), tp, tp});
     tp += v.size();
   }
   for (auto& g : ng) {
     auto& v = g.second;
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
-    b->noise_groups.push_back({g.first.bf16, g.first.block, (int)v.size(), tp});
+    b->noise_groups.push_back({g.first.bf16, g.first.block, g.first.nom, (int)v.size(), tp});
     tp += v.size();
   }
   c += al256(sizeof(Tile) * tiles_total);
@@ -1071,7 +1086,8 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
   for (int it = 0; it < n_iters && status == MPPI_OK; ++it) {
     cudaEventRecord(ev[0], s);
     for (const auto& g : b->noise_groups)
-      if (launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s) != cudaSuccess) status = MPPI_ERR_CUDA;
+      if (launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom) != cudaSuccess)
+        status = MPPI_ERR_CUDA;
     cudaEventRecord(ev[1], s);
     for (int obj = 0; obj < 3; ++obj) {
       for (const auto& g : b->rollout_groups)

@@ -95,6 +95,8 @@ struct SolveDesc {
   int32_t n_tiles, block;
   int32_t ext_noise;    // 1: use the caller's noise for this solve
   int32_t noise_gen;    // MPPI_NOISEGEN_*: where the normals are drawn
+  int32_t nominal_sample;  // 1: sample 0 carries no perturbation
+  int32_t warm_keep;    // 1: the next nominal is the whole new sequence (no shift)
 };
 
 // device-side per-launch inputs and outputs (indexed by the solve's position

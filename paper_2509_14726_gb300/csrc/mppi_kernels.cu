@@ -220,7 +220,9 @@ uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_ca
 // ---------------------------------------------------------------------------
 // K1: noise
 // ---------------------------------------------------------------------------
-template <int BF16>
+// NOM: the launch holds solves whose sample 0 is the unperturbed nominal
+// (a separate instance, so that the common launch carries no test for it)
+template <int BF16, int NOM>
 __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __restrict__ descs,
                                                           const Tile* __restrict__ tiles) {
   const Tile tile = tiles[blockIdx.x];
@@ -230,6 +232,20 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
   if (d.ext_noise || m >= K || threadIdx.x >= d.block) return;
   const uint32_t iter = d.st->iter;
   const bool five = d.nu == 5;
+  if (NOM && m == 0 && d.nominal_sample) {
+    // the nominal candidate (Eq. 3 with du = 0) is stored as zero normals
+    for (int k = 0; k < N; ++k) {
+      const size_t idx = (size_t)k * K;
+      if (BF16) {
+        d.Zb[idx] = make_uint2(0u, 0u);
+        if (five) d.Z5b[idx] = __float2bfloat16_rn(0.f);
+      } else {
+        d.Z4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (five) d.Z5[idx] = 0.f;
+      }
+    }
+    return;
+  }
 #pragma unroll kNoiseUnroll
   for (int k = 0; k < N; ++k) {
     const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
@@ -285,6 +301,10 @@ __device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int
   if (five) {
     const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
     z5 = box_muller(x5.x, x5.y).x;
+  }
+  if (m == 0 && d.nominal_sample) {  // Eq. 3 with du = 0
+    v = make_float4(0.f, 0.f, 0.f, 0.f);
+    z5 = 0.f;
   }
   if (BF16) {
     __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
@@ -961,10 +981,12 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     }
     __syncthreads();
     __threadfence();
-    // warm start: shift by one, repeat the last row over the whole capacity
+    // warm start: shift by one (or keep the sequence), repeat the last row
+    // over the whole capacity
+    const int shift = d.warm_keep ? 0 : 1;
     for (int o = tid; o < d.N_cap * kNU; o += blockDim.x) {
       const int k = o / kNU, j = o - k * kNU;
-      const int src = min(k + 1, N - 1);
+      const int src = min(k + shift, N - 1);
       d.U[o] = d.unew[src * kNU + j];
     }
     if (tid < kNX) st->prev_x0[tid] = x0s[tid];
@@ -1123,13 +1145,15 @@ unsigned long long launches_so_far() { return g_launches; }
 void add_launches(int n) { g_launches += (unsigned long long)n; }
 
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
-                         cudaStream_t s) {
+                         cudaStream_t s, int nominal) {
   if (n_tiles <= 0) return cudaSuccess;
   (void)cudaGetLastError();
   if (bf16)
-    noise_kernel<1><<<n_tiles, block, 0, s>>>(descs, tiles);
+    nominal ? noise_kernel<1, 1><<<n_tiles, block, 0, s>>>(descs, tiles)
+            : noise_kernel<1, 0><<<n_tiles, block, 0, s>>>(descs, tiles);
   else
-    noise_kernel<0><<<n_tiles, block, 0, s>>>(descs, tiles);
+    nominal ? noise_kernel<0, 1><<<n_tiles, block, 0, s>>>(descs, tiles)
+            : noise_kernel<0, 0><<<n_tiles, block, 0, s>>>(descs, tiles);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -32,8 +32,9 @@ cudaError_t configure_kernels();
 // largest block the rollout kernel was compiled for
 int rollout_max_block();
 
+// nominal: every solve of the launch has nominal_sample set (sample 0 is stored as zeros)
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
-                         cudaStream_t s);
+                         cudaStream_t s, int nominal);
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
                            int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen);
 cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s);

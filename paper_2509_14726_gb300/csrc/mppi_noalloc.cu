@@ -194,6 +194,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.drone_id = p.drone_id;
   d.noise_bf16 = bf16;
   d.noise_gen = p.noise_gen;
+  d.nominal_sample = p.nominal_sample ? 1 : 0;
+  d.warm_keep = p.warm_start == MPPI_WARM_KEEP ? 1 : 0;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -256,7 +258,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, block);
   add_launches(2);
   if (cudaGetLastError() != cudaSuccess) return fail(MPPI_ERR_CUDA, "set-up kernel launch failed");
-  if (d.noise_gen == MPPI_NOISEGEN_KERNEL && launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s) != cudaSuccess)
+  if (d.noise_gen == MPPI_NOISEGEN_KERNEL &&
+      launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s, d.nominal_sample) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "noise kernel launch failed");
   LaunchIO io;
   memset(&io, 0, sizeof io);

@@ -515,7 +515,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   // tiles: rollout groups by (objective, noise type, block), longest
   // horizons first; the noise launches reuse the same tiles per (type, block)
   struct Group {
-    int obj, bf16, block, gen;
+    int obj, bf16, block, gen, nom;
     std::vector<Tile> t;
     uint32_t smem = 0;
   };
@@ -529,10 +529,10 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     int g = -1;
     for (size_t q = 0; q < groups.size(); ++q)
       if (groups[q].obj == dd.objective && groups[q].bf16 == dd.noise_bf16 && groups[q].block == dd.block &&
-          groups[q].gen == dd.noise_gen)
+          groups[q].gen == dd.noise_gen && groups[q].nom == dd.nominal_sample)
         g = (int)q;
     if (g < 0) {
-      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, {}, 0});
+      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, dd.nominal_sample, {}, 0});
       g = (int)groups.size() - 1;
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * dd.block});
@@ -562,7 +562,8 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   io.status = sl.d_status;
   for (size_t q = 0; q < groups.size(); ++q)
     if (groups[q].gen == MPPI_NOISEGEN_KERNEL)
-      SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm));
+      SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm,
+                       groups[q].nom));
   for (size_t q = 0; q < groups.size(); ++q)
     SCU(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
                        groups[q].block, groups[q].smem, io, stm, groups[q].gen));

@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("temporal_rule", I32), ("q_lag", F), ("q_cont", F), ("q_omega", F * 3), ("r_dv", F),
                 ("r_dthrust", F), ("mu", F), ("v_theta_max", F), ("theta_back", F), ("theta_ahead", F),
                 ("Q", F * 13), ("QN", F * 13), ("R", F * 4), ("noise_dtype", I32), ("accum", I32), ("block", I32),
-                ("N_cap", I32), ("K_cap", I32), ("noise_gen", I32)]
+                ("N_cap", I32), ("K_cap", I32), ("noise_gen", I32), ("nominal_sample", I32), ("warm_start", I32)]
 
 
 class TrackC(C.Structure):
@@ -177,6 +177,7 @@ def make_params(sc: W.SolveConfig, noise_dtype: int = NOISE_F32, accum: int = AC
     p.R[:] = list(sc.R)
     p.noise_dtype, p.accum, p.block, p.N_cap, p.K_cap = noise_dtype, accum, block, N_cap, K_cap
     p.noise_gen = NOISEGEN_DEFAULT if noise_gen is None else noise_gen
+    p.nominal_sample, p.warm_start = int(sc.nominal_sample), int(sc.warm_start)
     return p
 
 

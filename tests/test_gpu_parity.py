@@ -371,3 +371,81 @@ def test_set_shape_changes_K_and_N(O, M):
     r = ora.solve(case.x0, 0.0)
     compare(gpu, r, "after set_shape")
     gpu.close()
+
+
+@pytest.mark.parametrize("objective", [0, 1, 2])
+@pytest.mark.parametrize("K", [8192, 2048])
+def test_paper_table1_size(O, M, objective, K):
+    """The paper's simulation parameters (Table I): 8192 samples (2048 on its
+    onboard computer), horizon 20, dt 0.03, temperature 0.01 -- a much sharper
+    weighting than lambda = 1; the conditioning-aware tolerance of the nominal
+    scales with it."""
+    mc, sc, tr, x0 = W.paper_table1(objective, K)
+    case = f32_case(mc, sc, tr, x0)
+    gpu, ora = make_pair(case)
+    t0 = 0.21
+    x = case.x0
+    if objective == 2:
+        x = np.float32(O.ref_eval(case.tr, t0)).astype(np.float64)
+        x[0:3] += 0.1
+    gpu.solve(x, t0)
+    r = ora.solve(x, t0)
+    st = compare(gpu, r, f"Table I size, K {K}, objective {objective}")
+    print(f"\nTable I K={K} objective {objective}: {st}")
+    gpu.close()
+
+
+@pytest.mark.parametrize("variant", [{"nominal_sample": 1}, {"warm_start": 1}, {"temporal_rule": 2},
+                                     {"temporal_rule": 0}, {"nominal_sample": 1, "warm_start": 1}],
+                         ids=["nominal_candidate", "warm_keep", "same_index_rule", "no_rule", "both"])
+def test_gate_logic_variants(O, M, variant):
+    """Variants of the sampling, the warm start and the temporal rule, over a
+    short closed-loop sequence (GPU started from the oracle's state at every
+    step): per-sample costs and gate decisions, the update, and the next
+    nominal (U*_new shifted by one step, or kept whole)."""
+    mc, sc, tr, x0 = W.c2_full_scale(0)
+    sc.K, sc.N = 2048, 30
+    for k, v in variant.items():
+        setattr(sc, k, v)
+    case = f32_case(mc, sc, tr, x0)
+    gpu, ora = make_pair(case)
+    x = case.x0.copy()
+    for step in range(3):
+        push_oracle_state(gpu, ora)
+        xs = np.float32(x).astype(np.float64)
+        gpu.solve(xs, 0.02 * step)
+        r = ora.solve(xs, 0.02 * step)
+        compare(gpu, r, f"variant {variant} step {step}")
+        unew = gpu.unew()
+        expect = unew if sc.warm_start == 1 else np.vstack([unew[1:], unew[-1:]])
+        np.testing.assert_array_equal(gpu.nominal(), expect)
+        x = O.rk4_step(case.mc, x, r["u0"][:4], sc.dt)
+    gpu.close()
+
+
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
+def test_batch_mixing_variants_equals_alone(M, use_graph):
+    """A plan mixing solves with and without the nominal candidate and with
+    either warm start gives each solve exactly what it gets alone."""
+    items = W.c3_batch(n_drones=8, K_lo=300, K_hi=2000, N_lo=5, N_hi=30)
+    pairs = []
+    for i, it in enumerate(items):
+        sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id,
+                           nominal_sample=i % 2, warm_start=(i // 2) % 2)
+        case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
+        pairs.append((M.Controller(case.mc, case.sc, case.tr), M.Controller(case.mc, case.sc, case.tr), case))
+    X0 = np.array([c.x0 for _, _, c in pairs])
+    b = M.mppi_batch_create([g1.h for g1, _, _ in pairs], use_graph=use_graph)
+    for rep in range(2):
+        ub, _ = M.mppi_batch_solve(b, len(pairs), X0, np.full(len(pairs), 0.3))
+        for i, (g1, g2, c) in enumerate(pairs):
+            ua, _ = g2.solve(c.x0, 0.3)
+            np.testing.assert_array_equal(ub[i], ua)
+            np.testing.assert_array_equal(g1.costs(), g2.costs())
+            np.testing.assert_array_equal(g1.nominal(), g2.nominal())
+            if c.sc.nominal_sample:
+                assert np.all(g1.noise()[:, 0, :] == 0)
+    M.mppi_batch_destroy(b)
+    for g1, g2, _ in pairs:
+        g1.close()
+        g2.close()
