@@ -36,6 +36,14 @@
  *     reading of Sec. III-B;
  *   - nominal_sample 1 makes candidate 0 the unperturbed nominal (Eq. 3 with
  *     du = 0), a common MPPI variant the paper does not use.
+ *   - rotor model (kind 1, Eq. 2 as printed): u = dT_s/dt per rotor, held
+ *     over the step; the thrusts follow T0 + u t exactly and saturate in
+ *     [thrust_min, thrust_max] (Table I: [0, 10] N, rates [-10, 10]); RK4
+ *     takes the exact stage thrusts (T is not integrated); l = 0.15 m and
+ *     c_tau = 0.01 m (not given); the rotor thrusts at x0 are the
+ *     controller's own integrated commands (hover until set); U starts at 0;
+ *     tracking weighs the rates themselves, contouring the rotor thrust
+ *     changes T_{k+1} - T_k.
  *
  * Parity status: every function here is pinned by a CPU test against a
  * closed form, an invariant, a brute-force search or an independent library
@@ -63,6 +71,13 @@ typedef struct {
   double u_max[5];
   double omega_max;   /* body-rate bound used by the feasibility penalty */
   double z_floor;     /* lowest altitude allowed by the penalty */
+  /* input parameterisation: 0 collective thrust + body-rate command (CTBR),
+   * 1 rotor-thrust rates u = dT/dt (Eq. 2 as printed) with the torque map
+   * tau = (l/sqrt2 (T1+T2-T3-T4), l/sqrt2 (-T1+T2+T3-T4), c_tau (T1-T2+T3-T4)) */
+  int32_t kind;
+  double arm;         /* l, m */
+  double c_tau;       /* rotor drag-torque coefficient, m */
+  double thrust_min, thrust_max; /* rotor thrust range, N (the thrust saturates) */
 } or_model;
 
 typedef struct {
@@ -113,6 +128,8 @@ typedef struct {
   int32_t has_prev;
   double theta, v_theta, c_last;
   int32_t has_theta;
+  double rotor[4];    /* rotor thrusts at x0 (rotor model): the controller's own */
+  int32_t has_rotor;  /* integrated commands; hover thrust until set */
 } or_state;
 
 typedef struct {
@@ -196,7 +213,8 @@ static void quat_to_R(const double q[4], double R[9]) {
   R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-void or_deriv(const or_model* md, const double x[13], const double u[4], double dx[13]) {
+/* Eq. 2 for a collective thrust c along body z and a body torque tau */
+static void rigid_deriv(const or_model* md, const double x[13], double c, const double tau[3], double dx[13]) {
   const double* v = x + 3; const double* q = x + 6; const double* w = x + 10;
   double R[9];
   quat_to_R(q, R);
@@ -207,7 +225,7 @@ void or_deriv(const or_model* md, const double x[13], const double u[4], double 
   for (int i = 0; i < 3; ++i) Rtv[i] = R[0 * 3 + i] * v[0] + R[1 * 3 + i] * v[1] + R[2 * 3 + i] * v[2];
   for (int i = 0; i < 3; ++i) DRtv[i] = md->drag[i] * Rtv[i];
   for (int i = 0; i < 3; ++i) {
-    double thrust = R[i * 3 + 2] * u[0] / md->mass;
+    double thrust = R[i * 3 + 2] * c / md->mass;
     double drag = R[i * 3 + 0] * DRtv[0] + R[i * 3 + 1] * DRtv[1] + R[i * 3 + 2] * DRtv[2];
     dx[3 + i] = thrust - drag;
   }
@@ -217,13 +235,35 @@ void or_deriv(const or_model* md, const double x[13], const double u[4], double 
   dx[7] = 0.5 * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
   dx[8] = 0.5 * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
   dx[9] = 0.5 * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
-  /* omega_dot = J^-1 (tau - omega x J omega), tau = J k_w (w_cmd - omega) */
+  /* omega_dot = J^-1 (tau - omega x J omega) */
   const double* Jd = md->inertia;
   double Jw[3] = {Jd[0] * w[0], Jd[1] * w[1], Jd[2] * w[2]};
   double cx[3] = {w[1] * Jw[2] - w[2] * Jw[1], w[2] * Jw[0] - w[0] * Jw[2], w[0] * Jw[1] - w[1] * Jw[0]};
-  for (int i = 0; i < 3; ++i) {
-    double tau = Jd[i] * md->k_omega * (u[1 + i] - w[i]);
-    dx[10 + i] = (tau - cx[i]) / Jd[i];
+  for (int i = 0; i < 3; ++i) dx[10 + i] = (tau[i] - cx[i]) / Jd[i];
+}
+
+/* CTBR: u = (c, w_cmd), body-rate loop tau = J k_w (w_cmd - omega) */
+void or_deriv(const or_model* md, const double x[13], const double u[4], double dx[13]) {
+  const double* w = x + 10;
+  double tau[3];
+  for (int i = 0; i < 3; ++i) tau[i] = md->inertia[i] * md->k_omega * (u[1 + i] - w[i]);
+  rigid_deriv(md, x, u[0], tau, dx);
+}
+
+/* Rotor model: collective thrust sum T_s and the torque map of Eq. 2 */
+void or_deriv_rotor(const or_model* md, const double x[13], const double T[4], double dx[13]) {
+  const double a = md->arm / sqrt(2.0);
+  const double tau[3] = {a * (T[0] + T[1] - T[2] - T[3]), a * (-T[0] + T[1] + T[2] - T[3]),
+                         md->c_tau * (T[0] - T[1] + T[2] - T[3])};
+  rigid_deriv(md, x, T[0] + T[1] + T[2] + T[3], tau, dx);
+}
+
+/* Rotor thrusts a time t after T0 at the rates u (dT/dt = u held over the
+ * step), saturating in [thrust_min, thrust_max]: the exact solution. */
+void or_rotor_at(const or_model* md, const double T0[4], const double u[4], double t, double T[4]) {
+  for (int s = 0; s < 4; ++s) {
+    double v = T0[s] + u[s] * t;
+    T[s] = v < md->thrust_min ? md->thrust_min : (v > md->thrust_max ? md->thrust_max : v);
   }
 }
 
@@ -243,6 +283,28 @@ void or_rk4_step(const or_model* md, const double x[13], const double u[4], doub
     double n = sqrt(xn[6] * xn[6] + xn[7] * xn[7] + xn[8] * xn[8] + xn[9] * xn[9]);
     for (int i = 6; i < 10; ++i) xn[i] /= n;
   }
+}
+
+/* One RK4 step of the rigid body with the rotor model: the stage thrusts
+ * are the exact rotor thrusts at the stage times (T is not integrated). */
+void or_rk4_step_rotor(const or_model* md, const double x[13], const double T0[4], const double u[4], double h,
+                       int renormalise, double xn[13], double Tn[4]) {
+  double k1[13], k2[13], k3[13], k4[13], xs[13], Th[4], T1[4];
+  or_rotor_at(md, T0, u, 0.5 * h, Th);
+  or_rotor_at(md, T0, u, h, T1);
+  or_deriv_rotor(md, x, T0, k1);
+  for (int i = 0; i < 13; ++i) xs[i] = x[i] + 0.5 * h * k1[i];
+  or_deriv_rotor(md, xs, Th, k2);
+  for (int i = 0; i < 13; ++i) xs[i] = x[i] + 0.5 * h * k2[i];
+  or_deriv_rotor(md, xs, Th, k3);
+  for (int i = 0; i < 13; ++i) xs[i] = x[i] + h * k3[i];
+  or_deriv_rotor(md, xs, T1, k4);
+  for (int i = 0; i < 13; ++i) xn[i] = x[i] + (h / 6.0) * (k1[i] + 2.0 * (k2[i] + k3[i]) + k4[i]);
+  if (renormalise) {
+    double n = sqrt(xn[6] * xn[6] + xn[7] * xn[7] + xn[8] * xn[8] + xn[9] * xn[9]);
+    for (int i = 6; i < 10; ++i) xn[i] /= n;
+  }
+  for (int s = 0; s < 4; ++s) Tn[s] = T1[s];
 }
 
 /* Feasibility penalty ("external cost", Sec. III-B) on one state. */
@@ -395,14 +457,19 @@ static int32_t prev_at(const or_ctx* cx, int32_t k) {
   return cx->prev[cx->n_prev - 1];
 }
 
-/* Rolls out one control sequence U[N][5] from x0 and scores it.  Returns J;
- * fills the optional diagnostics.  X (optional) receives [N+1][13]. */
+/* Rolls out one control sequence U[N][5] from x0 (and, for the rotor model,
+ * the rotor thrusts T0) and scores it.  Returns J; fills the optional
+ * diagnostics.  X (optional) receives [N+1][13], Trot [N+1][4]. */
 static double rollout_cost(const or_model* md, const or_params* pr, const or_track* tr,
-                           const or_ctx* cx, const double x0[13], const double* U,
+                           const or_ctx* cx, const double x0[13], const double* T0, const double* U,
                            double* Jabs_out, int32_t* npass_out, int32_t* first_out,
-                           int32_t* flag_out, int32_t* passcnt_out, double* X) {
+                           int32_t* flag_out, int32_t* passcnt_out, double* X, double* Trot) {
   int32_t N = pr->N;
   double x[13], xn[13];
+  const int rotor = md->kind == 1;
+  double Tk[4] = {0.0, 0.0, 0.0, 0.0}, Tk1[4] = {0.0, 0.0, 0.0, 0.0};  /* rotor thrusts at steps k, k+1 */
+  if (rotor) memcpy(Tk, T0, sizeof Tk);
+  if (Trot) memcpy(Trot, Tk, sizeof Tk);
   memcpy(x, x0, sizeof x);
   if (X) memcpy(X, x0, sizeof x);
   double J = 0.0, Jabs = 0.0;
@@ -414,7 +481,10 @@ static double rollout_cost(const or_model* md, const or_params* pr, const or_tra
   if (passcnt_out) passcnt_out[0] = 0;
   for (int32_t k = 0; k < N; ++k) {
     const double* u = U + OR_NU * k;
-    or_rk4_step(md, x, u, pr->dt, 1, xn);
+    if (rotor)
+      or_rk4_step_rotor(md, x, Tk, u, pr->dt, 1, xn, Tk1);
+    else
+      or_rk4_step(md, x, u, pr->dt, 1, xn);
     double pen = or_penalty(md, pr, xn);
     double stage = 0.0;
     if (pr->objective == 0) {
@@ -460,7 +530,15 @@ static double rollout_cost(const or_model* md, const or_params* pr, const or_tra
       double om = pr->q_omega[0] * xn[10] * xn[10] + pr->q_omega[1] * xn[11] * xn[11] +
                   pr->q_omega[2] * xn[12] * xn[12];
       double dv = pr->r_dv * a * a;
-      double dT = pr->r_dthrust * (u[0] - c_prev) * (u[0] - c_prev);
+      /* thrust change: collective command (CTBR) or the rotor thrusts */
+      double dT;
+      if (rotor) {
+        dT = 0.0;
+        for (int s = 0; s < 4; ++s) dT += (Tk1[s] - Tk[s]) * (Tk1[s] - Tk[s]);
+        dT *= pr->r_dthrust;
+      } else {
+        dT = pr->r_dthrust * (u[0] - c_prev) * (u[0] - c_prev);
+      }
       double prog = pr->mu * v1;
       stage = lag + con + om + dv + dT - prog;
       Jabs += lag + con + om + dv + dT + fabs(prog);
@@ -470,7 +548,8 @@ static double rollout_cost(const or_model* md, const or_params* pr, const or_tra
        * terminal error on x_N with Q_N. */
       const double* xr = cx->xref + 13 * k;
       double es = track_err(x, xr, pr->Q);
-      double hover = md->mass * md->gravity;
+      /* input effort: about hover (CTBR), the thrust rates themselves (rotor) */
+      double hover = rotor ? 0.0 : md->mass * md->gravity;
       double du[4] = {u[0] - hover, u[1], u[2], u[3]};
       double eu = pr->R[0] * du[0] * du[0] + pr->R[1] * du[1] * du[1] + pr->R[2] * du[2] * du[2] +
                   pr->R[3] * du[3] * du[3];
@@ -481,7 +560,9 @@ static double rollout_cost(const or_model* md, const or_params* pr, const or_tra
     J += stage + pen;
     Jabs += pen;
     memcpy(x, xn, sizeof x);
+    if (rotor) memcpy(Tk, Tk1, sizeof Tk);
     if (X) memcpy(X + 13 * (k + 1), x, sizeof x);
+    if (Trot) memcpy(Trot + 4 * (k + 1), Tk, sizeof Tk);
     if (passcnt_out) passcnt_out[k + 1] = passed;
   }
   if (Jabs_out) *Jabs_out = Jabs;
@@ -521,10 +602,14 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
     for (int j = 0; j < OR_NU; ++j) {
       double v;
       if (st->n_nom > 0) v = st->U[OR_NU * (k < st->n_nom ? k : st->n_nom - 1) + j];
-      else v = (j == 0) ? hover : 0.0;
+      else v = (j == 0 && md->kind != 1) ? hover : 0.0;  /* hover thrust (CTBR), zero rates (rotor) */
       Unom[OR_NU * k + j] = v;
     }
   }
+
+  /* rotor thrusts at x0 (rotor model): the controller's integrated commands */
+  double T0[4];
+  for (int s = 0; s < 4; ++s) T0[s] = st->has_rotor ? st->rotor[s] : 0.25 * hover;
 
   or_ctx cx;
   memset(&cx, 0, sizeof cx);
@@ -580,7 +665,8 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
     /* rollout and objective for this sample (Algorithm 1 inner loop) */
     double jabs;
     int32_t np, fp, fl;
-    J[m] = rollout_cost(md, pr, tr, &cx, x0, Us + (size_t)m * N * OR_NU, &jabs, &np, &fp, &fl, NULL, NULL);
+    J[m] = rollout_cost(md, pr, tr, &cx, x0, T0, Us + (size_t)m * N * OR_NU, &jabs, &np, &fp, &fl, NULL, NULL,
+                        NULL);
     if (out && out->J) out->J[m] = J[m];
     if (out && out->Jabs) out->Jabs[m] = jabs;
     if (out && out->npass) out->npass[m] = np;
@@ -633,7 +719,7 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
    * temporal rule (and the predicted trajectory) */
   int32_t* pc = (int32_t*)malloc(sizeof(int32_t) * (N + 1));
   double* Xn = (double*)malloc(sizeof(double) * 13 * (N + 1));
-  rollout_cost(md, pr, tr, &cx, x0, Unew, NULL, NULL, NULL, NULL, pc, Xn);
+  rollout_cost(md, pr, tr, &cx, x0, T0, Unew, NULL, NULL, NULL, NULL, pc, Xn, NULL);
   if (out && out->passcnt) memcpy(out->passcnt, pc, sizeof(int32_t) * (N + 1));
   if (out && out->Xnom) memcpy(out->Xnom, Xn, sizeof(double) * 13 * (N + 1));
 
@@ -657,6 +743,11 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
     st->has_theta = 1;
   }
   st->c_last = Unew[0];
+  if (md->kind == 1) {
+    /* the plant applies u0 (rotor-thrust rates) for one control period */
+    or_rotor_at(md, T0, Unew, pr->dt, st->rotor);
+    st->has_rotor = 1;
+  }
   memcpy(st->prev_x0, x0, sizeof(double) * 13);
   st->has_prev = 1;
   st->iter += 1;
@@ -670,10 +761,10 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
 double or_rollout(const or_model* md, const or_params* pr, const or_track* tr, const double x0[13],
                   const double* U, int32_t gate0, const int32_t* prev, int32_t n_prev,
                   double theta0, double vth0, double c_last, const double* xref,
-                  double* X, int32_t* passcnt) {
+                  double* X, int32_t* passcnt, const double* T0, double* Trot) {
   or_ctx cx;
   memset(&cx, 0, sizeof cx);
   cx.gate0 = gate0; cx.prev = prev; cx.n_prev = n_prev;
   cx.theta0 = theta0; cx.vth0 = vth0; cx.c_last = c_last; cx.xref = xref;
-  return rollout_cost(md, pr, tr, &cx, x0, U, NULL, NULL, NULL, NULL, passcnt, X);
+  return rollout_cost(md, pr, tr, &cx, x0, T0, U, NULL, NULL, NULL, NULL, passcnt, X, Trot);
 }

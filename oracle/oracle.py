@@ -27,7 +27,8 @@ PI = C.POINTER(C.c_int32)
 
 class OrModel(C.Structure):
     _fields_ = [("mass", D), ("inertia", D * 3), ("gravity", D), ("k_omega", D), ("drag", D * 3),
-                ("u_min", D * 5), ("u_max", D * 5), ("omega_max", D), ("z_floor", D)]
+                ("u_min", D * 5), ("u_max", D * 5), ("omega_max", D), ("z_floor", D), ("kind", I32), ("arm", D),
+                ("c_tau", D), ("thrust_min", D), ("thrust_max", D)]
 
 
 class OrParams(C.Structure):
@@ -47,7 +48,7 @@ class OrTrack(C.Structure):
 class OrState(C.Structure):
     _fields_ = [("U", PD), ("n_nom", I32), ("cap", I32), ("iter", U32), ("gate", I32), ("prevcnt", PI),
                 ("n_prev", I32), ("prev_x0", D * 13), ("has_prev", I32), ("theta", D), ("v_theta", D),
-                ("c_last", D), ("has_theta", I32)]
+                ("c_last", D), ("has_theta", I32), ("rotor", D * 4), ("has_rotor", I32)]
 
 
 class OrOut(C.Structure):
@@ -91,7 +92,10 @@ def lib():
                                C.POINTER(OrState), PD, D, C.POINTER(OrOut)]
         L.or_solve.restype = C.c_int
         L.or_rollout.argtypes = [C.POINTER(OrModel), C.POINTER(OrParams), C.POINTER(OrTrack), PD, PD, I32,
-                                 PI, I32, D, D, D, PD, PD, PI]
+                                 PI, I32, D, D, D, PD, PD, PI, PD, PD]
+        L.or_deriv_rotor.argtypes = [C.POINTER(OrModel), PD, PD, PD]
+        L.or_rotor_at.argtypes = [C.POINTER(OrModel), PD, PD, D, PD]
+        L.or_rk4_step_rotor.argtypes = [C.POINTER(OrModel), PD, PD, PD, D, C.c_int, PD, PD]
         L.or_rollout.restype = D
         _lib = L
     return _lib
@@ -122,6 +126,9 @@ def make_model(mc) -> OrModel:
     m.drag[:] = list(mc.drag)
     m.u_min[:] = list(mc.u_min)
     m.u_max[:] = list(mc.u_max)
+    m.kind = int(getattr(mc, "kind", 0))
+    m.arm, m.c_tau = getattr(mc, "arm", 0.15), getattr(mc, "c_tau", 0.01)
+    m.thrust_min, m.thrust_max = getattr(mc, "thrust_min", 0.0), getattr(mc, "thrust_max", 10.0)
     m.omega_max = mc.omega_max
     m.z_floor = mc.z_floor
     return m
@@ -206,6 +213,31 @@ def rk4_step(mc, x, u, h, renormalise=True) -> np.ndarray:
     return xn
 
 
+def deriv_rotor(mc, x, T) -> np.ndarray:
+    m = make_model(mc)
+    x, T = _f64(x), _f64(T)
+    dx = np.zeros(13)
+    lib().or_deriv_rotor(C.byref(m), _pd(x), _pd(T), _pd(dx))
+    return dx
+
+
+def rotor_at(mc, T0, u, t) -> np.ndarray:
+    m = make_model(mc)
+    T0, u = _f64(T0), _f64(u)
+    T = np.zeros(4)
+    lib().or_rotor_at(C.byref(m), _pd(T0), _pd(u), float(t), _pd(T))
+    return T
+
+
+def rk4_step_rotor(mc, x, T0, u, h, renormalise=True):
+    """One RK4 step of the rotor model; returns (x_next, T_next)."""
+    m = make_model(mc)
+    x, T0, u = _f64(x), _f64(T0), _f64(u)
+    xn, Tn = np.zeros(13), np.zeros(4)
+    lib().or_rk4_step_rotor(C.byref(m), _pd(x), _pd(T0), _pd(u), float(h), int(renormalise), _pd(xn), _pd(Tn))
+    return xn, Tn
+
+
 def penalty(mc, sc, x) -> float:
     m, p = make_model(mc), make_params(sc)
     x = _f64(x)
@@ -239,8 +271,11 @@ def ref_eval(track, t) -> np.ndarray:
     return xr
 
 
-def rollout(mc, sc, track, x0, U, gate0=0, prev=None, theta0=0.0, vth0=0.0, c_last=None, xref=None):
-    """Rolls one sequence U[N][5] out from x0; returns (J, X[N+1][13], passcnt[N+1])."""
+def rollout(mc, sc, track, x0, U, gate0=0, prev=None, theta0=0.0, vth0=0.0, c_last=None, xref=None, T0=None,
+            want_T=False):
+    """Rolls one sequence U[N][5] out from x0 (and rotor thrusts T0 for the
+    rotor model); returns (J, X[N+1][13], passcnt[N+1]) (+ T[N+1][4] with
+    want_T)."""
     m, p, tv = make_model(mc), make_params(sc), TrackView(track)
     N = sc.N
     U = _f64(np.asarray(U).reshape(N, -1))
@@ -254,8 +289,15 @@ def rollout(mc, sc, track, x0, U, gate0=0, prev=None, theta0=0.0, vth0=0.0, c_la
     if c_last is None:
         c_last = mc.mass * mc.gravity
     xr = _f64(xref) if xref is not None else np.zeros((N + 1, 13))
+    if T0 is None:
+        T0 = np.full(4, 0.25 * mc.mass * mc.gravity)
+    T0 = _f64(T0)
+    Tr = np.zeros((N + 1, 4))
     J = lib().or_rollout(C.byref(m), C.byref(p), C.byref(tv.c), _pd(x0), _pd(U), int(gate0), _pi(prev_a),
-                         int(n_prev), float(theta0), float(vth0), float(c_last), _pd(xr), _pd(X), _pi(pc))
+                         int(n_prev), float(theta0), float(vth0), float(c_last), _pd(xr), _pd(X), _pi(pc),
+                         _pd(T0), _pd(Tr))
+    if want_T:
+        return J, X, pc, Tr
     return J, X, pc
 
 
@@ -281,12 +323,16 @@ class OracleController:
         st.theta = st.v_theta = 0.0
         st.c_last = mc.mass * mc.gravity
         st.has_theta = 0
+        st.has_rotor = 0
         self.st = st
 
     # state access, so a test can start both sides from the same state
     def set_state(self, U=None, n_nom=None, iter=None, gate=None, prevcnt=None, prev_x0=None,
-                  theta=None, v_theta=None, c_last=None, has_theta=None):
+                  theta=None, v_theta=None, c_last=None, has_theta=None, rotor=None):
         st = self.st
+        if rotor is not None:
+            st.rotor[:] = [float(v) for v in rotor]
+            st.has_rotor = 1
         if U is not None:
             U = np.asarray(U, float)
             self.U[:] = 0.0
@@ -346,6 +392,13 @@ class OracleController:
     @property
     def nominal(self) -> np.ndarray:
         return self.U[: self.st.n_nom].copy()
+
+    @property
+    def rotor(self) -> np.ndarray:
+        """Rotor thrusts the next solve starts from (rotor model)."""
+        if self.st.has_rotor:
+            return np.array(list(self.st.rotor))
+        return np.full(4, 0.25 * self.mc.mass * self.mc.gravity)
 
     @property
     def gate(self) -> int:

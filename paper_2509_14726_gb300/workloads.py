@@ -57,6 +57,11 @@ class ModelConfig:
     u_max: Tuple[float, ...] = (4 * MASS * GRAVITY, 10.0, 10.0, 10.0, 20.0)
     omega_max: float = 10.0
     z_floor: float = 0.0
+    kind: int = 0              # 0: collective thrust + body rates, 1: rotor-thrust rates
+    arm: float = 0.15          # rotor model: arm length l, m
+    c_tau: float = 0.01        # rotor model: drag-torque coefficient, m
+    thrust_min: float = 0.0    # rotor model: per-rotor thrust range, N (Table I)
+    thrust_max: float = 10.0
 
     @property
     def hover(self) -> float:
@@ -401,6 +406,19 @@ def c2_full_scale(objective: int = OBJ_GATE, seed: int = 7):
     tr = random_course(seed, 7)
     cfg = SolveConfig(objective=objective, K=4096, N=50, dt=0.02, lam=1.0, seed=0)
     return ModelConfig(), cfg, tr, hover_state_before_gate(tr.gates, 0, 1.0)
+
+
+def rotor_model() -> ModelConfig:
+    """The input parameterisation of Eq. 2 as printed: rotor-thrust rates
+    u = dT_s/dt in [-10, 10] per rotor and thrusts T_s in [0, 10] N (Table I);
+    the 5th input (progress acceleration, contouring) keeps its range."""
+    return ModelConfig(kind=1, u_min=(-10.0, -10.0, -10.0, -10.0, -20.0), u_max=(10.0, 10.0, 10.0, 10.0, 20.0))
+
+
+def rotor_solve(sc: SolveConfig) -> SolveConfig:
+    """A solve configuration for the rotor model: the same weights, noise of
+    5 N/s per rotor rate (Table I gives the range, not the spread)."""
+    return dataclasses.replace(sc, sigma=(5.0, 5.0, 5.0, 5.0, sc.sigma[4]))
 
 
 def paper_table1(objective: int = OBJ_GATE, K: int = 8192, seed: int = 7):

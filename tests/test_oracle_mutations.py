@@ -26,7 +26,7 @@ MUTATIONS = [
      "dx[7] = 0.5 * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);",
      "dx[7] = 0.5 * (q[0] * w[0] - q[2] * w[2] + q[3] * w[1]);"),
     ("gyroscopic term sign",
-     "dx[10 + i] = (tau - cx[i]) / Jd[i];", "dx[10 + i] = (tau + cx[i]) / Jd[i];"),
+     "dx[10 + i] = (tau[i] - cx[i]) / Jd[i];", "dx[10 + i] = (tau[i] + cx[i]) / Jd[i];"),
     ("drag applied in the world frame",
      "for (int i = 0; i < 3; ++i) DRtv[i] = md->drag[i] * Rtv[i];",
      "for (int i = 0; i < 3; ++i) DRtv[i] = md->drag[i] * v[i];"),
@@ -51,6 +51,18 @@ MUTATIONS = [
      "pr->warm_start == 1 ? k :", "pr->warm_start == 1 ? (k + 1 < N ? k + 1 : N - 1) :"),
     ("nominal candidate perturbed like the others",
      "if (pr->nominal_sample && m == 0) {", "if (pr->nominal_sample && m < 0) {"),
+    ("rotor roll torque pattern mirrored",
+     "a * (T[0] + T[1] - T[2] - T[3])", "a * (T[0] - T[1] - T[2] + T[3])"),
+    ("rotor yaw torque pattern of the roll axis",
+     "md->c_tau * (T[0] - T[1] + T[2] - T[3])", "md->c_tau * (T[0] + T[1] - T[2] - T[3])"),
+    ("rotor thrust does not saturate",
+     "T[s] = v < md->thrust_min ? md->thrust_min : (v > md->thrust_max ? md->thrust_max : v);", "T[s] = v;"),
+    ("rotor stage 2 uses the start-of-step thrusts",
+     "or_deriv_rotor(md, xs, Th, k2);", "or_deriv_rotor(md, xs, T0, k2);"),
+    ("rotor tracking effort about hover",
+     "double hover = rotor ? 0.0 : md->mass * md->gravity;", "double hover = md->mass * md->gravity;"),
+    ("rotor state not advanced by u0",
+     "or_rotor_at(md, T0, Unew, pr->dt, st->rotor);", "or_rotor_at(md, T0, Unew, 0.0, st->rotor);"),
     ("samples not clamped",
      "u[j] = clampd(Unom[OR_NU * k + j] + pr->sigma[j] * z[j], md->u_min[j], md->u_max[j]);",
      "u[j] = Unom[OR_NU * k + j] + pr->sigma[j] * z[j];"),

@@ -712,3 +712,133 @@ def test_nonfinite_costs_get_zero_weight(oracle_mod):
     r = ctl.solve(x_bad, 0.0)
     assert r["status"] == 1
     np.testing.assert_allclose(r["Unew"][:, 0], mc.hover)
+
+
+# ---------------------------------------------------------------------------
+# the rotor-thrust-rate model (Eq. 2 as printed: u = dT_s/dt, torque map)
+# ---------------------------------------------------------------------------
+
+def _rotor_mc(**kw):
+    mc = W.rotor_model()
+    for k, v in kw.items():
+        setattr(mc, k, v)
+    return mc
+
+
+def test_rotor_hover_is_an_equilibrium(oracle_mod):
+    mc = _rotor_mc()
+    x = _state(p=(1, -2, 3), q=W.yaw_quat(0.7))
+    T = np.full(4, mc.hover / 4)
+    x1, T1 = x.copy(), T.copy()
+    for _ in range(50):
+        x1, T1 = oracle_mod.rk4_step_rotor(mc, x1, T1, np.zeros(4), 0.02)
+    np.testing.assert_allclose(x1, x, atol=1e-12)
+    np.testing.assert_array_equal(T1, T)
+
+
+def test_rotor_free_fall_is_exact(oracle_mod):
+    mc = _rotor_mc()
+    x = _state(p=(0, 0, 50), v=(1, 2, 3))
+    T = np.zeros(4)
+    h, n = 0.05, 20
+    for _ in range(n):
+        x, T = oracle_mod.rk4_step_rotor(mc, x, T, np.zeros(4), h)
+    t = h * n
+    np.testing.assert_allclose(x[:3], [t, 2 * t, 50 + 3 * t - 0.5 * mc.gravity * t * t], atol=1e-11)
+    np.testing.assert_allclose(x[3:6], [1, 2, 3 - mc.gravity * t], atol=1e-12)
+
+
+def test_rotor_thrust_ramp_is_exact(oracle_mod):
+    """Level attitude, all rotors ramping at the same rate r from a: the
+    collective thrust 4 (a + r t) is linear in t, so v_z is quadratic and p_z
+    cubic -- RK4 with the exact stage thrusts reproduces both exactly."""
+    mc = _rotor_mc()
+    a, r, m, g = 1.5, 2.0, mc.mass, mc.gravity
+    x = _state(p=(0, 0, 5))
+    T = np.full(4, a)
+    h, n = 0.03, 40
+    for _ in range(n):
+        x, T = oracle_mod.rk4_step_rotor(mc, x, T, np.full(4, r), h)
+    t = h * n
+    vz = (4 * a / m - g) * t + 2 * r * t * t / m
+    pz = 5 + 0.5 * (4 * a / m - g) * t * t + 2 * r * t ** 3 / (3 * m)
+    assert abs(x[5] - vz) < 1e-11 and abs(x[2] - pz) < 1e-11
+    np.testing.assert_allclose(T, a + r * t, atol=1e-12)
+
+
+def test_rotor_thrust_saturates_in_its_range(oracle_mod):
+    mc = _rotor_mc()
+    T0 = np.array([9.0, 0.5, 5.0, 9.9])
+    u = np.array([10.0, -10.0, 0.0, 10.0])
+    for t, expect in ((0.04, [9.4, 0.1, 5.0, 10.0]), (0.1, [10.0, 0.0, 5.0, 10.0]), (0.5, [10.0, 0.0, 5.0, 10.0])):
+        np.testing.assert_allclose(oracle_mod.rotor_at(mc, T0, u, t), expect, atol=1e-15)
+
+
+@pytest.mark.parametrize("pattern,axis", [((1, 1, -1, -1), 0), ((-1, 1, 1, -1), 1), ((1, -1, 1, -1), 2)])
+def test_rotor_torque_map(oracle_mod, pattern, axis):
+    """Differential thrust patterns of the torque map in Eq. 2: each excites
+    one body axis only; the collective thrust is the rotor sum."""
+    mc = _rotor_mc()
+    a, d = 2.0, 0.3
+    T = a + d * np.asarray(pattern, float)
+    dx = oracle_mod.deriv_rotor(mc, _state(), T)
+    l2 = mc.arm / math.sqrt(2.0)
+    tau = [l2 * 4 * d, l2 * 4 * d, mc.c_tau * 4 * d][axis]
+    expect = np.zeros(3)
+    expect[axis] = tau / mc.inertia[axis]
+    np.testing.assert_allclose(dx[10:13], expect, atol=1e-14)
+    assert abs(dx[5] - (4 * a / mc.mass - mc.gravity)) < 1e-14
+
+
+def test_rotor_yaw_spin_up(oracle_mod):
+    """A constant yaw torque from rest: omega_z grows linearly (exact) and
+    the attitude follows the yaw angle psi = alpha t^2 / 2 (RK4 order)."""
+    mc = _rotor_mc()
+    a, d = mc.hover / 4, 0.2
+    T = a + d * np.array([1.0, -1.0, 1.0, -1.0])
+    alpha = 4 * mc.c_tau * d / mc.inertia[2]
+    x = _state()
+    h, n = 0.01, 30
+    for _ in range(n):
+        x, T = oracle_mod.rk4_step_rotor(mc, x, T, np.zeros(4), h)
+    t = h * n
+    assert abs(x[12] - alpha * t) < 1e-12
+    psi = 0.5 * alpha * t * t
+    np.testing.assert_allclose(x[6:10], [math.cos(psi / 2), 0, 0, math.sin(psi / 2)], atol=1e-9)
+
+
+def test_rotor_tracking_effort_is_on_the_rates(oracle_mod):
+    """Tracking a reference that is the rollout of a known rate sequence: the
+    cost is sum ||u||^2_R on the rates themselves (no hover offset)."""
+    mc = _rotor_mc()
+    N, h = 10, 0.03
+    rng = np.random.default_rng(8)
+    U = np.zeros((N, 5))
+    U[:, :4] = rng.normal(0, 3.0, (N, 4))
+    x0 = _state(p=(1, 2, 3), q=W.yaw_quat(-0.3))
+    T0 = np.array([2.0, 2.2, 1.9, 2.1])
+    sc = W.SolveConfig(objective=2, K=1, N=N, dt=h)
+    _, X, _, Tr = oracle_mod.rollout(mc, sc, _line_track(), x0, U, T0=T0, want_T=True)
+    np.testing.assert_allclose(Tr[1], T0 + U[0, :4] * h, atol=1e-14)
+    xref = np.vstack([X])
+    J, _, _ = oracle_mod.rollout(mc, sc, _line_track(), x0, U, xref=xref, T0=T0)
+    expect = float(np.sum(np.asarray(sc.R) * U[:, :4] ** 2))
+    assert abs(J - expect) < 1e-9
+
+
+def test_rotor_controller_state(oracle_mod):
+    """The nominal starts at zero rates (Algorithm 1's U = 0) and the rotor
+    thrusts advance by the applied u0 over one control period."""
+    mc = _rotor_mc()
+    _, sc, tr, x0 = W.c1_single_gate()
+    sc = W.rotor_solve(sc)
+    sc.K, sc.N = 32, 6
+    ctl = oracle_mod.OracleController(mc, sc, tr)
+    T0 = ctl.rotor.copy()
+    np.testing.assert_allclose(T0, mc.hover / 4)
+    r = ctl.solve(x0, 0.0, want_Z=True)
+    us = np.clip(np.asarray(sc.sigma) * r["Z"].transpose(1, 0, 2), mc.u_min, mc.u_max)
+    us[:, :, 4] = 0
+    np.testing.assert_allclose(r["Unew"], np.einsum("m,mkj->kj", r["w"], us), atol=1e-12)
+    np.testing.assert_allclose(ctl.rotor, np.clip(T0 + r["u0"][:4] * sc.dt, mc.thrust_min, mc.thrust_max),
+                               atol=1e-14)
