@@ -79,10 +79,17 @@ enum { MPPI_WARM_SHIFT = 0, MPPI_WARM_KEEP = 1 };
 #define MPPI_MAX_N 128     /* longest horizon a handle may use */
 #define MPPI_MAX_GATES 64  /* most gates a track may have */
 
-/* Quadrotor model (Eq. 2).  kind selects the input parameterisation; only
- * MPPI_MODEL_CTBR (collective thrust + body-rate command, body-rate loop
- * tau = J k_omega (w_cmd - w)) is implemented; ROTOR_RATE is rejected with
- * MPPI_ERR_ARG. */
+/* Quadrotor model (Eq. 2).  kind selects the input parameterisation:
+ *   MPPI_MODEL_CTBR: u = (collective thrust, body-rate command); body-rate
+ *     loop tau = J k_omega (w_cmd - w);
+ *   MPPI_MODEL_ROTOR_RATE: u = dT_s/dt, the rates of the four rotor thrusts
+ *     (Eq. 2 as printed).  The thrusts are state: they follow T + u t over a
+ *     step and saturate in [thrust_min, thrust_max]; collective thrust =
+ *     T1+T2+T3+T4, torque = (l/sqrt2 (T1+T2-T3-T4), l/sqrt2 (-T1+T2+T3-T4),
+ *     c_tau (T1-T2+T3-T4)).  x0 stays 13-D: the rotor thrusts at x0 are the
+ *     handle's own integrated commands (hover thrust until set, see
+ *     mppi_set_rotor_thrusts).  u_min / u_max bound the rates; k_omega is
+ *     unused.  Needs MPPI_NOISE_F32 storage. */
 typedef struct {
   int32_t kind;
   float mass;         /* kg */
@@ -94,6 +101,10 @@ typedef struct {
   float u_max[5];
   float omega_max;    /* body-rate bound of the feasibility penalty */
   float z_floor;      /* altitude floor of the feasibility penalty */
+  float arm;          /* rotor model: arm length l, m */
+  float c_tau;        /* rotor model: rotor drag-torque coefficient, m */
+  float thrust_min;   /* rotor model: per-rotor thrust range, N */
+  float thrust_max;
 } mppi_model_t;
 
 /* Sampling, objective and weighting parameters (Eq. 3-9, Table I). */
@@ -239,6 +250,11 @@ int mppi_get_xref(mppi_handle h, float* xref);
  * thrust).  With buf == NULL, *size receives the byte count. */
 int mppi_export_state(mppi_handle h, void* buf, size_t* size);
 int mppi_import_state(mppi_handle h, const void* buf, size_t size);
+/* Rotor model: the rotor thrusts [4] (N) that the next solve starts from
+ * (e.g. measured); get returns the current ones.  MPPI_ERR_ARG for a
+ * collective-thrust handle. */
+int mppi_set_rotor_thrusts(mppi_handle h, const float T[4]);
+int mppi_get_rotor_thrusts(mppi_handle h, float T[4]);
 int mppi_set_gate_index(mppi_handle h, int32_t gate);
 
 /* Uses caller-provided standard normals for the next solve instead of
@@ -265,6 +281,11 @@ int mppi_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_
  * d_x0 [13], d_U [B][N][4] -> d_X [B][N+1][13].  For model tests. */
 int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B,
                         const float* d_x0, const float* d_U, float* d_X, void* stream);
+/* The same for the rotor model (Eq. 2 as printed): d_x0 [13], d_T0 [B][4]
+ * start thrusts, d_U [B][N][4] thrust rates -> d_X [B][N+1][13] and the
+ * thrusts d_T [B][N+1][4].  MPPI_ERR_ARG for a collective-thrust model. */
+int mppi_rollout_states_rotor(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
+                              const float* d_T0, const float* d_U, float* d_X, float* d_T, void* stream);
 
 /* A solve for callers that cannot allocate device memory while they run.
  * The paper has no counterpart: this is an interface for integration.
@@ -300,7 +321,8 @@ int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t 
  * clears what must start at zero.  Calls whose work overlaps on the GPU (two
  * streams, or two threads) race on the array and give wrong results: issue
  * them on one stream, or order them.  Asynchronous: returns after enqueueing
- * on `stream`.  Errors: MPPI_ERR_ARG (null pointer, bad sizes, scratch limit),
+ * on `stream`.  Errors: MPPI_ERR_ARG (null pointer, bad sizes, scratch limit, a
+ * rotor-thrust-rate model: its rotor thrusts are handle state),
  * MPPI_ERR_CUDA. */
 int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t* params, const mppi_track_t* d_track,
                        const float* d_x0, double t0, const float* d_U, uint32_t iter, int32_t gate,

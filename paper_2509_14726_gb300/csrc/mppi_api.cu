@@ -133,7 +133,7 @@ struct mppi_batch_s {
   int n = 0;
   SolveDesc* d_descs = nullptr;
   struct Group {
-    int objective, bf16, block, gen, nom;  // gen: MPPI_NOISEGEN_*; nom: nominal candidate
+    int objective, bf16, block, gen, nom, rot;  // gen: MPPI_NOISEGEN_*; nom: nominal candidate; rot: rotor model
     uint32_t smem;
     int n_tiles;
     Tile* d_tiles;
@@ -172,8 +172,13 @@ namespace {
 
 int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* t) {
   if (!m || !p || !t) return fail(MPPI_ERR_ARG, "null model, params or track");
-  if (m->kind != MPPI_MODEL_CTBR)
-    return fail(MPPI_ERR_ARG, "model kind %d not implemented (only collective thrust + body rate)", m->kind);
+  if (m->kind != MPPI_MODEL_CTBR && m->kind != MPPI_MODEL_ROTOR_RATE)
+    return fail(MPPI_ERR_ARG, "unknown model kind %d", m->kind);
+  if (m->kind == MPPI_MODEL_ROTOR_RATE) {
+    if (!(m->arm > 0) || !(m->c_tau >= 0) || !(m->thrust_max > m->thrust_min))
+      return fail(MPPI_ERR_ARG, "rotor model needs arm > 0, c_tau >= 0 and thrust_max > thrust_min");
+    if (p && p->noise_dtype != MPPI_NOISE_F32) return fail(MPPI_ERR_ARG, "the rotor model uses float32 noise storage");
+  }
   if (!(m->mass > 0) || !(m->inertia[0] > 0) || !(m->inertia[1] > 0) || !(m->inertia[2] > 0))
     return fail(MPPI_ERR_ARG, "mass and inertia must be positive");
   if (p->K < 1 || p->N < 1 || p->N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K=%d N=%d out of range", p->K, p->N);
@@ -297,6 +302,12 @@ void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int 
   }
   for (int i = 0; i < 4; ++i) d.R[i] = p.R[i];
   d.hover = m.mass * m.gravity;
+  d.rotor = m.kind == MPPI_MODEL_ROTOR_RATE ? 1 : 0;
+  d.arm2 = (float)((double)m.arm / sqrt(2.0));
+  d.c_tau = m.c_tau;
+  d.thrust_min = m.thrust_min;
+  d.thrust_max = m.thrust_max;
+  for (int i = 0; i < 3; ++i) d.inv_J[i] = (float)(1.0 / (double)m.inertia[i]);
 }
 
 namespace {
@@ -318,8 +329,10 @@ int upload_tiles(mppi_handle h) {
   return MPPI_OK;
 }
 
+// initial nominal: hover thrust (collective-thrust model) or zero rotor-thrust rates
 void fill_hover(const mppi_handle h, std::vector<float>& U) {
   U.assign((size_t)h->N_cap * kNU + 8, 0.f);
+  if (h->model.kind == MPPI_MODEL_ROTOR_RATE) return;
   for (int k = 0; k < h->N_cap; ++k) U[(size_t)k * kNU] = h->model.mass * h->model.gravity;
 }
 
@@ -362,6 +375,10 @@ int mppi_default_model(mppi_model_t* m) {
   }
   m->omega_max = 10.f;
   m->z_floor = 0.f;
+  m->arm = 0.15f;
+  m->c_tau = 0.01f;
+  m->thrust_min = 0.f;
+  m->thrust_max = 10.f;
   return MPPI_OK;
 }
 
@@ -578,7 +595,8 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
   }
   const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, h->block, merge_cap(d.n_tiles));
-  CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen));
+  CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen,
+                    d.rotor));
   return MPPI_OK;
 }
 
@@ -757,6 +775,26 @@ int mppi_set_gate_index(mppi_handle h, int32_t gate) {
   return MPPI_OK;
 }
 
+int mppi_set_rotor_thrusts(mppi_handle h, const float T[4]) {
+  if (!h || !T) return fail(MPPI_ERR_ARG, "null argument");
+  if (!h->hd.rotor) return fail(MPPI_ERR_ARG, "not a rotor-model handle");
+  DevState st;
+  CU(cudaMemcpy(&st, h->hd.st, sizeof st, cudaMemcpyDeviceToHost));
+  for (int r = 0; r < 4; ++r) st.rotor[r] = T[r];
+  st.has_rotor = 1;
+  CU(cudaMemcpy(h->hd.st, &st, sizeof st, cudaMemcpyHostToDevice));
+  return MPPI_OK;
+}
+
+int mppi_get_rotor_thrusts(mppi_handle h, float T[4]) {
+  if (!h || !T) return fail(MPPI_ERR_ARG, "null argument");
+  if (!h->hd.rotor) return fail(MPPI_ERR_ARG, "not a rotor-model handle");
+  DevState st;
+  CU(cudaMemcpy(&st, h->hd.st, sizeof st, cudaMemcpyDeviceToHost));
+  for (int r = 0; r < 4; ++r) T[r] = st.has_rotor ? st.rotor[r] : 0.25f * h->hd.hover;
+  return MPPI_OK;
+}
+
 int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* stream) {
   if (!h || !d_Z) return fail(MPPI_ERR_ARG, "null argument");
   if (h->nu == 5 && !d_Z5) return fail(MPPI_ERR_ARG, "contouring needs the 5th noise column");
@@ -792,11 +830,16 @@ int mppi_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_
   return MPPI_OK;
 }
 
-int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
-                        const float* d_U, float* d_X, void* stream) {
-  if (!model || N < 1 || B < 0 || (B > 0 && (!d_x0 || !d_U || !d_X))) return fail(MPPI_ERR_ARG, "bad arguments");
+static int rollout_states_impl(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
+                               const float* d_U, float* d_X, void* stream, const float* d_T0, float* d_T) {
   SolveDesc md;
   memset(&md, 0, sizeof md);
+  md.rotor = model->kind == MPPI_MODEL_ROTOR_RATE ? 1 : 0;
+  md.arm2 = (float)((double)model->arm / sqrt(2.0));
+  md.c_tau = model->c_tau;
+  md.thrust_min = model->thrust_min;
+  md.thrust_max = model->thrust_max;
+  for (int i = 0; i < 3; ++i) md.inv_J[i] = (float)(1.0 / (double)model->inertia[i]);
   md.inv_mass = (float)(1.0 / (double)model->mass);
   md.gravity = model->gravity;
   md.k_omega = model->k_omega;
@@ -806,8 +849,23 @@ int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t 
   md.gyro[2] = (float)((Jy - Jx) / Jz);
   for (int i = 0; i < 3; ++i) md.drag[i] = model->drag[i];
   md.has_drag = (model->drag[0] != 0.f || model->drag[1] != 0.f || model->drag[2] != 0.f) ? 1 : 0;
-  CU(launch_rollout_states(md, dt, N, B, d_x0, d_U, d_X, static_cast<cudaStream_t>(stream)));
+  CU(launch_rollout_states(md, dt, N, B, d_x0, d_U, d_X, static_cast<cudaStream_t>(stream), d_T0, d_T));
   return MPPI_OK;
+}
+
+int mppi_rollout_states(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
+                        const float* d_U, float* d_X, void* stream) {
+  if (!model || N < 1 || B < 0 || (B > 0 && (!d_x0 || !d_U || !d_X))) return fail(MPPI_ERR_ARG, "bad arguments");
+  if (model->kind != MPPI_MODEL_CTBR) return fail(MPPI_ERR_ARG, "rotor model: use mppi_rollout_states_rotor");
+  return rollout_states_impl(model, dt, N, B, d_x0, d_U, d_X, stream, nullptr, nullptr);
+}
+
+int mppi_rollout_states_rotor(const mppi_model_t* model, float dt, int32_t N, int32_t B, const float* d_x0,
+                              const float* d_T0, const float* d_U, float* d_X, float* d_T, void* stream) {
+  if (!model || N < 1 || B < 0 || (B > 0 && (!d_x0 || !d_T0 || !d_U || !d_X || !d_T)))
+    return fail(MPPI_ERR_ARG, "bad arguments");
+  if (model->kind != MPPI_MODEL_ROTOR_RATE) return fail(MPPI_ERR_ARG, "not a rotor model");
+  return rollout_states_impl(model, dt, N, B, d_x0, d_U, d_X, stream, d_T0, d_T);
 }
 
 // ---------------------------------------------------------------------------
@@ -828,7 +886,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     CU(cudaStreamWaitEvent(bs, b->fork, 0));
     if (g.gen == MPPI_NOISEGEN_KERNEL)
       CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs, g.nom));
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen, g.rot));
     CU(cudaEventRecord(b->join[i], bs));
     CU(cudaStreamWaitEvent(s, b->join[i], 0));
   }
@@ -838,7 +896,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom));
   for (const auto& g : b->rollout_groups)
-    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen));
+    CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen, g.rot));
   return MPPI_OK;
 }
 
@@ -876,13 +934,14 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   b->branches = use_graph == 1;
   // group tiles by launch configuration; longest horizons first (LPT)
   struct Key {
-    int obj, bf16, block, gen, nom;
+    int obj, bf16, block, gen, nom, rot;
     bool operator<(const Key& o) const {
       if (obj != o.obj) return obj < o.obj;
       if (bf16 != o.bf16) return bf16 < o.bf16;
       if (block != o.block) return block < o.block;
       if (gen != o.gen) return gen < o.gen;
-      return nom < o.nom;
+      if (nom != o.nom) return nom < o.nom;
+      return rot < o.rot;
     }
   };
   std::vector<std::pair<Key, std::vector<Tile>>> rg;
@@ -899,8 +958,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
     const SolveDesc& d = hs[i]->hd;
-    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen, d.nominal_sample};
-    Key kn{0, d.noise_bf16, d.block, 0, d.nominal_sample};
+    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen, d.nominal_sample, d.rotor};
+    Key kn{0, d.noise_bf16, d.block, 0, d.nominal_sample, 0};
     auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
       for (size_t j = 0; j < v.size(); ++j)
         if (!(v[j].first < key) && !(key < v[j].first)) return (int)j;
@@ -945,7 +1004,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if (cudaMemcpy(tp, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice))
       return cleanup(fail(MPPI_ERR_CUDA, "tile upload failed"));
     const Key& k = rg[gi].first;
-    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.gen, k.nom, rsmem[gi], (int)v.size(), tp, tp});
+    b->rollout_groups.push_back({k.obj, k.bf16, k.block, k.gen, k.nom, k.rot, rsmem[gi], (int)v.size(), tp, tp});
     tp += v.size();
   }
   for (auto& g : ng) {
@@ -1092,7 +1151,8 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
     for (int obj = 0; obj < 3; ++obj) {
       for (const auto& g : b->rollout_groups)
         if (g.objective == obj &&
-            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen) !=
+            launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen,
+                           g.rot) !=
                 cudaSuccess)
           status = MPPI_ERR_CUDA;
       cudaEventRecord(ev[2 + obj], s);

@@ -39,6 +39,10 @@ struct DevState {
   float c_last;        // last applied collective thrust
   float prev_x0[kNX];  // x0 of the last solve
   double scal[4];      // theta0, v_theta0, J_min, sum of exp weights
+  float rotor[4];      // rotor model: rotor thrusts at the next x0 (integrated commands)
+  float rotor_prev[4]; // rotor thrusts at the x0 of the last solve (its nominal rollout)
+  int32_t has_rotor;   // 0: hover thrust
+  int32_t pad_;
 };
 
 // --------------------------------------------------------------------------
@@ -97,6 +101,9 @@ struct SolveDesc {
   int32_t noise_gen;    // MPPI_NOISEGEN_*: where the normals are drawn
   int32_t nominal_sample;  // 1: sample 0 carries no perturbation
   int32_t warm_keep;    // 1: the next nominal is the whole new sequence (no shift)
+  // rotor-thrust-rate model (model kind MPPI_MODEL_ROTOR_RATE)
+  int32_t rotor;
+  float arm2, c_tau, thrust_min, thrust_max, inv_J[3];
 };
 
 // device-side per-launch inputs and outputs (indexed by the solve's position
@@ -315,6 +322,160 @@ __device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, f
   s.qx = qx1 * rn;
   s.qy = qy1 * rn;
   s.qz = qz1 * rn;
+}
+
+// Rotor-thrust-rate model (Eq. 2 as printed): four rotor thrusts with
+// dT/dt = u held over the step, saturating in [tmin, tmax]; collective
+// thrust = their sum; torque tau = (l/sqrt2 (T0+T1-T2-T3),
+// l/sqrt2 (-T0+T1+T2-T3), c_tau (T0-T1+T2-T3)).
+struct RotorRegs {
+  float arm2, c_tau, tmin, tmax;  // arm2 = l / sqrt(2)
+  float iJx, iJy, iJz;            // 1 / J
+};
+
+// twice the quaternion rate and the body-rate derivative J^-1 tau - J^-1 (w x J w)
+// for the torque accelerations (bx, by, bz) = J^-1 tau
+__device__ __forceinline__ void attitude_rate2_torque(const ModelRegs& M, float bx, float by, float bz, float qw,
+                                                      float qx, float qy, float qz, float wx, float wy, float wz,
+                                                      float& dqw, float& dqx, float& dqy, float& dqz, float& dwx,
+                                                      float& dwy, float& dwz) {
+  dqw = -(qx * wx + qy * wy + qz * wz);
+  dqx = qw * wx + qy * wz - qz * wy;
+  dqy = qw * wy + qz * wx - qx * wz;
+  dqz = qw * wz + qx * wy - qy * wx;
+  dwx = bx - M.g0 * wy * wz;
+  dwy = by - M.g1 * wz * wx;
+  dwz = bz - M.g2 * wx * wy;
+}
+
+// thrust terms of one set of rotor thrusts: 2 c/m, c/m - g and J^-1 tau.
+// The torque combinations are formed from pairwise differences of the
+// (nearly equal) thrusts, which are exact when the two are within a factor
+// of two, instead of differences of sums, which cancel.
+__device__ __forceinline__ void rotor_forces(const ModelRegs& M, const RotorRegs& R, float t0, float t1, float t2,
+                                             float t3, float& ac2, float& acg, float& bx, float& by, float& bz) {
+  const float ac = ((t0 + t1) + (t2 + t3)) * M.inv_mass;
+  ac2 = 2.f * ac;
+  acg = ac - M.gravity;
+  bx = R.arm2 * ((t0 - t2) + (t1 - t3)) * R.iJx;
+  by = R.arm2 * ((t1 - t0) + (t2 - t3)) * R.iJy;
+  bz = R.c_tau * ((t0 - t1) + (t2 - t3)) * R.iJz;
+}
+
+// One compensated step of a saturating thrust ramp: (T, c) holds T - c, the
+// increment y is added with Kahan's correction; a bound, when reached, is
+// exact (c = 0).  Returns the exact-as-possible change of the thrust.
+__device__ __forceinline__ float rotor_advance(float& T, float& c, float y, float tmin, float tmax) {
+  const float yc = y - c;
+  float t = T + yc;
+  float cn = (t - T) - yc;
+  if (t > tmax) { t = tmax; cn = 0.f; }
+  if (t < tmin) { t = tmin; cn = 0.f; }
+  const float d = (t - T) - (cn - c);
+  T = t;
+  c = cn;
+  return d;
+}
+
+// One classical RK4 step of the rotor model.  The stage thrusts are the exact
+// saturating ramps at t, t + h/2 and t + h (T is not integrated); the
+// thrusts (T, Tc: compensated, true value T - Tc) advance to the end of the
+// step.  dp receives the position increment, dT2 the squared thrust change
+// sum_s (T_s(t+h) - T_s(t))^2.
+template <bool DRAG>
+__device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRegs& R, Quad& s, float T[4],
+                                               float Tc[4], float u0, float u1, float u2, float u3, float h,
+                                               float& dpx, float& dpy, float& dpz, float& dT2) {
+  const float h2 = 0.5f * h, h4 = 0.25f * h;
+  const float t0 = T[0] - Tc[0], t1 = T[1] - Tc[1], t2 = T[2] - Tc[2], t3 = T[3] - Tc[3];
+  const float m0 = clampf(T[0] + (u0 * h2 - Tc[0]), R.tmin, R.tmax);
+  const float m1 = clampf(T[1] + (u1 * h2 - Tc[1]), R.tmin, R.tmax);
+  const float m2 = clampf(T[2] + (u2 * h2 - Tc[2]), R.tmin, R.tmax);
+  const float m3 = clampf(T[3] + (u3 * h2 - Tc[3]), R.tmin, R.tmax);
+  float e[4] = {T[0], T[1], T[2], T[3]}, ec[4] = {Tc[0], Tc[1], Tc[2], Tc[3]};
+  const float d0 = rotor_advance(e[0], ec[0], u0 * h, R.tmin, R.tmax);
+  const float d1 = rotor_advance(e[1], ec[1], u1 * h, R.tmin, R.tmax);
+  const float d2 = rotor_advance(e[2], ec[2], u2 * h, R.tmin, R.tmax);
+  const float d3 = rotor_advance(e[3], ec[3], u3 * h, R.tmin, R.tmax);
+  const float e0 = e[0] - ec[0], e1 = e[1] - ec[1], e2 = e[2] - ec[2], e3 = e[3] - ec[3];
+  float ac2, acg, bx, by, bz;
+  float dqw, dqx, dqy, dqz, dwx, dwy, dwz, ax, ay, az;
+  // stage 1 (start-of-step thrusts)
+  rotor_forces(M, R, t0, t1, t2, t3, ac2, acg, bx, by, bz);
+  attitude_rate2_torque(M, bx, by, bz, s.qw, s.qx, s.qy, s.qz, s.wx, s.wy, s.wz, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, s.qw, s.qx, s.qy, s.qz, s.vx, s.vy, s.vz, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, s.qw, s.qx, s.qy, s.qz, ax, ay, az);
+  float sqw = dqw, sqx = dqx, sqy = dqy, sqz = dqz, swx = dwx, swy = dwy, swz = dwz;
+  float sax = ax, say = ay, saz = az;
+  float pax = ax, pay = ay, paz = az;
+  float vx2 = 0.f, vy2 = 0.f, vz2 = 0.f;
+  // stages 2 and 3 (mid-step thrusts)
+  rotor_forces(M, R, m0, m1, m2, m3, ac2, acg, bx, by, bz);
+  float qw2 = s.qw + h4 * dqw, qx2 = s.qx + h4 * dqx, qy2 = s.qy + h4 * dqy, qz2 = s.qz + h4 * dqz;
+  float wx2 = s.wx + h2 * dwx, wy2 = s.wy + h2 * dwy, wz2 = s.wz + h2 * dwz;
+  if (DRAG) { vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az; }
+  attitude_rate2_torque(M, bx, by, bz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
+  sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
+  swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
+  sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
+  pax += ax; pay += ay; paz += az;
+  qw2 = s.qw + h4 * dqw; qx2 = s.qx + h4 * dqx; qy2 = s.qy + h4 * dqy; qz2 = s.qz + h4 * dqz;
+  wx2 = s.wx + h2 * dwx; wy2 = s.wy + h2 * dwy; wz2 = s.wz + h2 * dwz;
+  if (DRAG) { vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az; }
+  attitude_rate2_torque(M, bx, by, bz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
+  sqw += 2.f * dqw; sqx += 2.f * dqx; sqy += 2.f * dqy; sqz += 2.f * dqz;
+  swx += 2.f * dwx; swy += 2.f * dwy; swz += 2.f * dwz;
+  sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
+  pax += ax; pay += ay; paz += az;
+  // stage 4 (end-of-step thrusts)
+  rotor_forces(M, R, e0, e1, e2, e3, ac2, acg, bx, by, bz);
+  qw2 = s.qw + h2 * dqw; qx2 = s.qx + h2 * dqx; qy2 = s.qy + h2 * dqy; qz2 = s.qz + h2 * dqz;
+  wx2 = s.wx + h * dwx; wy2 = s.wy + h * dwy; wz2 = s.wz + h * dwz;
+  if (DRAG) { vx2 = s.vx + h * ax; vy2 = s.vy + h * ay; vz2 = s.vz + h * az; }
+  attitude_rate2_torque(M, bx, by, bz, qw2, qx2, qy2, qz2, wx2, wy2, wz2, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
+  if (DRAG)
+    accel_drag(M, ac2, acg, qw2, qx2, qy2, qz2, vx2, vy2, vz2, ax, ay, az);
+  else
+    accel_nodrag(ac2, acg, qw2, qx2, qy2, qz2, ax, ay, az);
+  sqw += dqw; sqx += dqx; sqy += dqy; sqz += dqz;
+  swx += dwx; swy += dwy; swz += dwz;
+  sax += ax; say += ay; saz += az;
+  // combine (the same form as the collective-thrust step)
+  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6, h12 = 0.5f * h6;
+  dpx = h * s.vx + hh6 * pax;
+  dpy = h * s.vy + hh6 * pay;
+  dpz = h * s.vz + hh6 * paz;
+  kahan_add(s.px, s.cpx, dpx);
+  kahan_add(s.py, s.cpy, dpy);
+  kahan_add(s.pz, s.cpz, dpz);
+  kahan_add(s.vx, s.cvx, h6 * sax);
+  kahan_add(s.vy, s.cvy, h6 * say);
+  kahan_add(s.vz, s.cvz, h6 * saz);
+  const float qw1 = s.qw + h12 * sqw, qx1 = s.qx + h12 * sqx, qy1 = s.qy + h12 * sqy, qz1 = s.qz + h12 * sqz;
+  s.wx += h6 * swx;
+  s.wy += h6 * swy;
+  s.wz += h6 * swz;
+  const float rn = rsqrtf(qw1 * qw1 + qx1 * qx1 + qy1 * qy1 + qz1 * qz1);
+  s.qw = qw1 * rn;
+  s.qx = qx1 * rn;
+  s.qy = qy1 * rn;
+  s.qz = qz1 * rn;
+  dT2 = d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    T[r] = e[r];
+    Tc[r] = ec[r];
+  }
 }
 
 // compensated position (hi - compensation)

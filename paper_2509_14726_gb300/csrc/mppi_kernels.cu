@@ -439,7 +439,8 @@ __device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int 
 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
 
-template <int OBJ, int BF16, int GEN>
+// ROT: rotor-thrust-rate input model (rotor thrusts in the state)
+template <int OBJ, int BF16, int GEN, int ROT>
 __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__ descs,
                                                             const Tile* __restrict__ tiles, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -614,6 +615,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   M.inv_mass = d.inv_mass; M.gravity = d.gravity; M.k_omega = d.k_omega;
   M.g0 = d.gyro[0]; M.g1 = d.gyro[1]; M.g2 = d.gyro[2];
   M.d0 = d.drag[0]; M.d1 = d.drag[1]; M.d2 = d.drag[2]; M.has_drag = d.has_drag;
+  RotorRegs RR;
+  RR.arm2 = d.arm2; RR.c_tau = d.c_tau; RR.tmin = d.thrust_min; RR.tmax = d.thrust_max;
+  RR.iJx = d.inv_J[0]; RR.iJy = d.inv_J[1]; RR.iJz = d.inv_J[2];
   float Jh = 0.f, Jc = 0.f;
   int passed = 0, first = -1;
   if (active) {
@@ -625,6 +629,14 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     s.qw = x0s[6]; s.qx = x0s[7]; s.qy = x0s[8]; s.qz = x0s[9];
     s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
     const float h = d.dt;
+    // rotor thrusts (rotor model): the controller's integrated commands
+    float Tr[4] = {0.f, 0.f, 0.f, 0.f}, Trc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ROT) {
+      const bool hr = st->has_rotor != 0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) Tr[r] = hr ? st->rotor[r] : 0.25f * d.hover;
+    }
+    float dT2 = 0.f;
     // objective state
     // gate progress state: target gate, p_k - g for it (ra), its plane distance
     int gi = 0, gate_start = 0, slot0 = 0;
@@ -694,7 +706,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         e = s.wx - xr[10]; stage += d.Q[10] * e * e;
         e = s.wy - xr[11]; stage += d.Q[11] * e * e;
         e = s.wz - xr[12]; stage += d.Q[12] * e * e;
-        const float du = u0 - d.hover;
+        const float du = ROT ? u0 : u0 - d.hover;  // rotor model: the rates themselves
         stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
       }
       float near = 0.f;
@@ -711,10 +723,17 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         near = d0 < r_near2 ? q_near * d0 : 0.f;
       }
       float dpx, dpy, dpz;
-      if (M.has_drag)
-        rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
-      else
-        rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+      if (ROT) {
+        if (M.has_drag)
+          rk4_step_rotor<true>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+        else
+          rk4_step_rotor<false>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+      } else {
+        if (M.has_drag)
+          rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+        else
+          rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+      }
       if (OBJ == MPPI_OBJ_GATE) {
         // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
         // with both positions taken relative to g before rounding
@@ -767,10 +786,12 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         const float ez = ((s.pz - A[2]) - fr * (Bn[2] - A[2])) - s.cpz;
         const float et = ex * Tx + ey * Ty + ez * Tz;
         const float cx = ex - et * Tx, cy = ey - et * Ty, cz = ez - et * Tz;
+        // thrust change: the collective command, or the rotor thrusts (rotor model)
         const float dT = u0 - c_prev;
+        const float dTT = ROT ? dT2 : dT * dT;
         stage = d.q_lag * et * et + d.q_cont * (cx * cx + cy * cy + cz * cz) +
                 d.q_omega[0] * s.wx * s.wx + d.q_omega[1] * s.wy * s.wy + d.q_omega[2] * s.wz * s.wz +
-                d.r_dv * a * a + d.r_dthrust * dT * dT - d.mu * v1;
+                d.r_dv * a * a + d.r_dthrust * dTT - d.mu * v1;
         c_prev = u0;
         vth = v1;
       } else {
@@ -1000,6 +1021,17 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       st->has_prev = 1;
       st->n_nom = N;
       st->c_last = c0;
+      if (ROT) {
+        // the plant applies u0 (rotor-thrust rates) for one control period
+        const bool hr = st->has_rotor != 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float t0r = hr ? st->rotor[r] : 0.25f * d.hover;
+          st->rotor_prev[r] = t0r;
+          st->rotor[r] = clampf(t0r + d.unew[r] * d.dt, d.thrust_min, d.thrust_max);
+        }
+        st->has_rotor = 1;
+      }
       if (OBJ == MPPI_OBJ_CONTOUR) {
         const float a0 = d.unew[4];
         st->theta = s_theta0;
@@ -1054,14 +1086,25 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
     GateF g = sG[w][gate_slot(gi, d.n_gates, d.closed)];
     float sa = plane_dist(g, s.px, s.py);
     d.passcnt[0] = 0;
+    RotorRegs RR;
+    RR.arm2 = d.arm2; RR.c_tau = d.c_tau; RR.tmin = d.thrust_min; RR.tmax = d.thrust_max;
+    RR.iJx = d.inv_J[0]; RR.iJy = d.inv_J[1]; RR.iJz = d.inv_J[2];
+    float Tr[4] = {st->rotor_prev[0], st->rotor_prev[1], st->rotor_prev[2], st->rotor_prev[3]};
+    float Trc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < N; ++k) {
       const float* u = d.unew + kNU * k;
       const float ax = pxt(s), ay = pyt(s), az = pzt(s);
-      float dpx, dpy, dpz;
-      if (M.has_drag)
+      float dpx, dpy, dpz, dT2;
+      if (d.rotor) {
+        if (M.has_drag)
+          rk4_step_rotor<true>(M, RR, s, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
+        else
+          rk4_step_rotor<false>(M, RR, s, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
+      } else if (M.has_drag) {
         rk4_step<true>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
-      else
+      } else {
         rk4_step<false>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+      }
       const float bx = pxt(s), by = pyt(s), bz = pzt(s);
       const float sb = plane_dist(g, bx, by);
       if (sa < 0.f && sb >= 0.f) {
@@ -1111,10 +1154,20 @@ __global__ void normals_kernel(uint32_t seed, uint32_t drone, uint32_t k, uint32
   reinterpret_cast<float4*>(out)[i] = normals4(seed, drone, (uint32_t)i, k, it, blk);
 }
 
-__global__ void rollout_states_kernel(ModelRegs M, float dt, int N, int B, const float* __restrict__ x0,
-                                      const float* __restrict__ U, float* __restrict__ X) {
+// rotor (rotor model): T0 [B][4] start thrusts, Tout [B][N+1][4] thrusts
+__global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, int rotor, float dt, int N, int B,
+                                      const float* __restrict__ x0, const float* __restrict__ U,
+                                      float* __restrict__ X, const float* __restrict__ T0,
+                                      float* __restrict__ Tout) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  float T[4] = {0.f, 0.f, 0.f, 0.f}, Tc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (rotor) {
+    for (int r = 0; r < 4; ++r) {
+      T[r] = T0[(size_t)b * 4 + r];
+      Tout[(size_t)b * (N + 1) * 4 + r] = T[r];
+    }
+  }
   Quad s;
   s.px = x0[0]; s.py = x0[1]; s.pz = x0[2]; s.cpx = s.cpy = s.cpz = 0.f;
   s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5]; s.cvx = s.cvy = s.cvz = 0.f;
@@ -1124,11 +1177,18 @@ __global__ void rollout_states_kernel(ModelRegs M, float dt, int N, int B, const
   for (int c = 0; c < kNX; ++c) o[c] = x0[c];
   for (int k = 0; k < N; ++k) {
     const float* u = U + ((size_t)b * N + k) * 4;
-    float dpx, dpy, dpz;
-    if (M.has_drag)
+    float dpx, dpy, dpz, dT2;
+    if (rotor) {
+      if (M.has_drag)
+        rk4_step_rotor<true>(M, R, s, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
+      else
+        rk4_step_rotor<false>(M, R, s, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
+      for (int c = 0; c < 4; ++c) Tout[((size_t)b * (N + 1) + k + 1) * 4 + c] = T[c] - Tc[c];
+    } else if (M.has_drag) {
       rk4_step<true>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
-    else
+    } else {
       rk4_step<false>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+    }
     float* r = o + (size_t)(k + 1) * kNX;
     r[0] = pxt(s); r[1] = pyt(s); r[2] = pzt(s);
     r[3] = s.vx - s.cvx; r[4] = s.vy - s.cvy; r[5] = s.vz - s.cvz;
@@ -1158,56 +1218,71 @@ cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles,
   return cudaGetLastError();
 }
 
-template <int OBJ, int BF16>
+template <int OBJ, int BF16, int ROT>
 static cudaError_t configure_t() {
-  cudaError_t e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 0, ROT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 1, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
   // drawing the noise again in the epilogue stores nothing, so it has no
   // bfloat16 form
   if constexpr (!BF16)
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(rollout_kernel<OBJ, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      e = cudaFuncSetAttribute(rollout_kernel<OBJ, 0, 2, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
   return e;
 }
 
 cudaError_t configure_kernels() {
   cudaError_t e;
-  if ((e = configure_t<MPPI_OBJ_GATE, 0>()) != cudaSuccess) return e;
-  if ((e = configure_t<MPPI_OBJ_GATE, 1>()) != cudaSuccess) return e;
-  if ((e = configure_t<MPPI_OBJ_CONTOUR, 0>()) != cudaSuccess) return e;
-  if ((e = configure_t<MPPI_OBJ_CONTOUR, 1>()) != cudaSuccess) return e;
-  if ((e = configure_t<MPPI_OBJ_TRACK, 0>()) != cudaSuccess) return e;
-  return configure_t<MPPI_OBJ_TRACK, 1>();
+  if ((e = configure_t<MPPI_OBJ_GATE, 0, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_GATE, 1, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_CONTOUR, 0, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_CONTOUR, 1, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_TRACK, 0, 0>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_TRACK, 1, 0>()) != cudaSuccess) return e;
+  // the rotor model is built with float32 noise storage only
+  if ((e = configure_t<MPPI_OBJ_GATE, 0, 1>()) != cudaSuccess) return e;
+  if ((e = configure_t<MPPI_OBJ_CONTOUR, 0, 1>()) != cudaSuccess) return e;
+  return configure_t<MPPI_OBJ_TRACK, 0, 1>();
 }
 
-template <int OBJ, int BF16>
+template <int OBJ, int BF16, int ROT>
 static cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
                                     uint32_t smem, LaunchIO io, cudaStream_t s, int gen) {
   (void)cudaGetLastError();
   if (gen == 2) {
     if constexpr (BF16) return cudaErrorInvalidValue;
-    else rollout_kernel<OBJ, 0, 2><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+    else rollout_kernel<OBJ, 0, 2, ROT><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   } else if (gen == 1) {
-    rollout_kernel<OBJ, BF16, 1><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+    rollout_kernel<OBJ, BF16, 1, ROT><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   } else {
-    rollout_kernel<OBJ, BF16, 0><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+    rollout_kernel<OBJ, BF16, 0, ROT><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   }
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
-                           int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen) {
+                           int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor) {
   if (n_tiles <= 0) return cudaSuccess;
+  if (rotor) {
+    if (bf16) return cudaErrorInvalidValue;
+    switch (objective) {
+      case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+      case 1: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+      case 2: return launch_rollout_t<MPPI_OBJ_TRACK, 0, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (objective * 2 + (bf16 ? 1 : 0)) {
-    case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
-    case 1: return launch_rollout_t<MPPI_OBJ_GATE, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
-    case 2: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
-    case 3: return launch_rollout_t<MPPI_OBJ_CONTOUR, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
-    case 4: return launch_rollout_t<MPPI_OBJ_TRACK, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
-    case 5: return launch_rollout_t<MPPI_OBJ_TRACK, 1>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 0: return launch_rollout_t<MPPI_OBJ_GATE, 0, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 1: return launch_rollout_t<MPPI_OBJ_GATE, 1, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 2: return launch_rollout_t<MPPI_OBJ_CONTOUR, 0, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 3: return launch_rollout_t<MPPI_OBJ_CONTOUR, 1, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 4: return launch_rollout_t<MPPI_OBJ_TRACK, 0, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
+    case 5: return launch_rollout_t<MPPI_OBJ_TRACK, 1, 0>(descs, tiles, n_tiles, block, smem, io, s, gen);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1239,14 +1314,17 @@ cudaError_t launch_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t i
 }
 
 cudaError_t launch_rollout_states(const SolveDesc& md, float dt, int N, int B, const float* x0, const float* U,
-                                  float* X, cudaStream_t s) {
+                                  float* X, cudaStream_t s, const float* T0, float* Tout) {
   if (B <= 0) return cudaSuccess;
   ModelRegs M;
   M.inv_mass = md.inv_mass; M.gravity = md.gravity; M.k_omega = md.k_omega;
   M.g0 = md.gyro[0]; M.g1 = md.gyro[1]; M.g2 = md.gyro[2];
   M.d0 = md.drag[0]; M.d1 = md.drag[1]; M.d2 = md.drag[2]; M.has_drag = md.has_drag;
+  RotorRegs R;
+  R.arm2 = md.arm2; R.c_tau = md.c_tau; R.tmin = md.thrust_min; R.tmax = md.thrust_max;
+  R.iJx = md.inv_J[0]; R.iJy = md.inv_J[1]; R.iJz = md.inv_J[2];
   (void)cudaGetLastError();
-  rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, dt, N, B, x0, U, X);
+  rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, R, md.rotor, dt, N, B, x0, U, X, T0, Tout);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -269,7 +269,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.u0 = d_u0;
   io.status = nullptr;
   const uint32_t smem = rollout_smem_bytes(p.N, p.objective, d.S, block, d.n_tiles > 32 ? d.n_tiles : 32);
-  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen) != cudaSuccess)
+  if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen, d.rotor) !=
+      cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");
   return MPPI_OK;
 }

@@ -292,7 +292,10 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   if (!s || !model || !params || !track || !drone_out) return sfail(MPPI_ERR_ARG, "null argument");
   std::lock_guard<std::mutex> lk(s->mu);
   if ((int)s->drones.size() >= s->max_drones) return sfail(MPPI_ERR_NOT_ADMITTED, "server holds max_drones drones");
-  if (model->kind != MPPI_MODEL_CTBR) return sfail(MPPI_ERR_ARG, "only the collective-thrust/body-rate model");
+  if (model->kind != MPPI_MODEL_CTBR && model->kind != MPPI_MODEL_ROTOR_RATE) return sfail(MPPI_ERR_ARG, "model kind");
+  if (model->kind == MPPI_MODEL_ROTOR_RATE &&
+      (params->noise_dtype != MPPI_NOISE_F32 || !(model->arm > 0) || !(model->thrust_max > model->thrust_min)))
+    return sfail(MPPI_ERR_ARG, "rotor model: float32 noise, arm > 0, thrust_max > thrust_min");
   const mppi_params_t& p = *params;
   const int block = p.block ? p.block : 128;
   if (block < 32 || block > std::min(128, rollout_max_block()) || block % 32)
@@ -374,7 +377,8 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   if (track->T > 0 && track->ref)
     SCU(cudaMemcpy((void*)h.ref, track->ref, sizeof(float) * 13 * track->T, cudaMemcpyHostToDevice));
   std::vector<float> U((size_t)N_cap * kNU + 8, 0.f);
-  for (int k = 0; k < N_cap; ++k) U[(size_t)k * kNU] = model->mass * model->gravity;
+  if (model->kind != MPPI_MODEL_ROTOR_RATE)  // hover thrust; the rotor model starts at zero rates
+    for (int k = 0; k < N_cap; ++k) U[(size_t)k * kNU] = model->mass * model->gravity;
   SCU(cudaMemcpy(h.U, U.data(), sizeof(float) * U.size(), cudaMemcpyHostToDevice));
   DevState st;
   memset(&st, 0, sizeof st);
@@ -515,7 +519,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   // tiles: rollout groups by (objective, noise type, block), longest
   // horizons first; the noise launches reuse the same tiles per (type, block)
   struct Group {
-    int obj, bf16, block, gen, nom;
+    int obj, bf16, block, gen, nom, rot;
     std::vector<Tile> t;
     uint32_t smem = 0;
   };
@@ -529,10 +533,10 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     int g = -1;
     for (size_t q = 0; q < groups.size(); ++q)
       if (groups[q].obj == dd.objective && groups[q].bf16 == dd.noise_bf16 && groups[q].block == dd.block &&
-          groups[q].gen == dd.noise_gen && groups[q].nom == dd.nominal_sample)
+          groups[q].gen == dd.noise_gen && groups[q].nom == dd.nominal_sample && groups[q].rot == dd.rotor)
         g = (int)q;
     if (g < 0) {
-      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, dd.nominal_sample, {}, 0});
+      groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, dd.nominal_sample, dd.rotor, {}, 0});
       g = (int)groups.size() - 1;
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * dd.block});
@@ -566,7 +570,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
                        groups[q].nom));
   for (size_t q = 0; q < groups.size(); ++q)
     SCU(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
-                       groups[q].block, groups[q].smem, io, stm, groups[q].gen));
+                       groups[q].block, groups[q].smem, io, stm, groups[q].gen, groups[q].rot));
   SCU(launch_nominal(ddesc, reinterpret_cast<const int32_t*>(sl.dev + st.which), (int)which.size(), stm));
   SCU(cudaEventRecord(sl.done, stm));
   sl.reqs.swap(batch);

@@ -37,7 +37,8 @@ class MppiError(RuntimeError):
 
 class Model(C.Structure):
     _fields_ = [("kind", I32), ("mass", F), ("inertia", F * 3), ("gravity", F), ("k_omega", F), ("drag", F * 3),
-                ("u_min", F * 5), ("u_max", F * 5), ("omega_max", F), ("z_floor", F)]
+                ("u_min", F * 5), ("u_max", F * 5), ("omega_max", F), ("z_floor", F), ("arm", F), ("c_tau", F),
+                ("thrust_min", F), ("thrust_max", F)]
 
 
 class Params(C.Structure):
@@ -92,6 +93,9 @@ def load():
         "mppi_export_state": ([vp, vp, C.POINTER(sz)], C.c_int),
         "mppi_import_state": ([vp, vp, sz], C.c_int),
         "mppi_set_gate_index": ([vp, I32], C.c_int),
+        "mppi_set_rotor_thrusts": ([vp, PF], C.c_int),
+        "mppi_rollout_states_rotor": ([C.POINTER(Model), F, I32, I32, vp, vp, vp, vp, vp, vp], C.c_int),
+        "mppi_get_rotor_thrusts": ([vp, PF], C.c_int),
         "mppi_set_noise": ([vp, vp, vp, vp], C.c_int),
         "mppi_philox": ([U32, U32, U32, U32, U32, U32, I32, vp, vp], C.c_int),
         "mppi_normals": ([U32, U32, U32, U32, U32, I32, vp, vp], C.c_int),
@@ -150,8 +154,9 @@ def _stream_ptr(stream) -> C.c_void_p:
 
 def make_model(mc: W.ModelConfig) -> Model:
     m = Model()
-    m.kind = 0
+    m.kind = int(mc.kind)
     m.mass, m.gravity, m.k_omega = mc.mass, mc.gravity, mc.k_omega
+    m.arm, m.c_tau, m.thrust_min, m.thrust_max = mc.arm, mc.c_tau, mc.thrust_min, mc.thrust_max
     m.inertia[:] = list(mc.inertia)
     m.drag[:] = list(mc.drag)
     m.u_min[:] = list(mc.u_min)
@@ -347,6 +352,23 @@ def mppi_set_gate_index(h: int, gate: int) -> None:
     _check(load().mppi_set_gate_index(C.c_void_p(h), int(gate)))
 
 
+def mppi_rollout_states_rotor(model: Model, dt: float, N: int, B: int, d_x0: int, d_T0: int, d_U: int, d_X: int,
+                              d_T: int, stream=None):
+    _check(load().mppi_rollout_states_rotor(C.byref(model), float(dt), N, B, C.c_void_p(d_x0), C.c_void_p(d_T0),
+                                            C.c_void_p(d_U), C.c_void_p(d_X), C.c_void_p(d_T), _stream_ptr(stream)))
+
+
+def mppi_set_rotor_thrusts(h: int, T) -> None:
+    a = (C.c_float * 4)(*[float(v) for v in T])
+    _check(load().mppi_set_rotor_thrusts(C.c_void_p(h), a))
+
+
+def mppi_get_rotor_thrusts(h: int) -> np.ndarray:
+    a = (C.c_float * 4)()
+    _check(load().mppi_get_rotor_thrusts(C.c_void_p(h), a))
+    return np.array(list(a), np.float32)
+
+
 def mppi_set_noise(h: int, d_Z: int, d_Z5: Optional[int], stream=None) -> None:
     _check(load().mppi_set_noise(C.c_void_p(h), C.c_void_p(d_Z), C.c_void_p(d_Z5 or 0), _stream_ptr(stream)))
 
@@ -428,6 +450,13 @@ class Controller:
         mppi_set_shape(self.h, K, N)
         self.K, self.N = K, N
 
+    def rotor_thrusts(self) -> np.ndarray:
+        """Rotor model: the rotor thrusts the next solve starts from."""
+        return mppi_get_rotor_thrusts(self.h)
+
+    def set_rotor_thrusts(self, T) -> None:
+        mppi_set_rotor_thrusts(self.h, T)
+
     def nominal(self):
         return mppi_get_nominal(self.h, self.N)
 
@@ -462,7 +491,8 @@ class Controller:
         mppi_import_state(self.h, blob)
 
 
-_DEVSTATE_FMT = "<10i2d14f4d"  # DevState: 10 int32, theta, v_theta, c_last + prev_x0[13], scal[4]
+# DevState: 10 int32, theta, v_theta, c_last + prev_x0[13], scal[4], rotor[4], rotor_prev[4], has_rotor, pad
+_DEVSTATE_FMT = "<10i2d14f4d8f2i"
 
 
 def decode_state(blob: bytes, N_cap: int) -> dict:
@@ -474,7 +504,8 @@ def decode_state(blob: bytes, N_cap: int) -> dict:
     d = {"gate": i32[0], "iter": i32[1] & 0xFFFFFFFF, "has_prev": i32[2], "has_theta": i32[3], "n_nom": i32[4],
          "n_prev": i32[5], "gate0": i32[6], "adv": i32[7], "status": i32[8], "timeouts": i32[9],
          "theta": vals[10], "v_theta": vals[11], "c_last": vals[12], "prev_x0": np.array(vals[13:26]),
-         "scal": np.array(vals[26:30]), "nu": nu}
+         "scal": np.array(vals[26:30]), "rotor": np.array(vals[30:34]), "rotor_prev": np.array(vals[34:38]),
+         "has_rotor": vals[38], "nu": nu}
     off = 16 + struct.calcsize(_DEVSTATE_FMT)
     d["U"] = np.frombuffer(blob, np.float32, count=N_cap * 5, offset=off).reshape(N_cap, 5).astype(np.float64)
     off += 4 * N_cap * 5
@@ -484,7 +515,7 @@ def decode_state(blob: bytes, N_cap: int) -> dict:
 
 def encode_state(N_cap: int, nu: int, U, iter: int = 0, gate: int = 0, prevcnt=None, prev_x0=None,
                  theta: float = 0.0, v_theta: float = 0.0, c_last: float = 0.0, has_theta: int = 0,
-                 n_nom: Optional[int] = None) -> bytes:
+                 n_nom: Optional[int] = None, rotor=None) -> bytes:
     """Builds a state blob for mppi_import_state.  U rows beyond its length
     repeat its last row; pass counts beyond theirs repeat the last count."""
     import struct
@@ -505,7 +536,9 @@ def encode_state(N_cap: int, nu: int, U, iter: int = 0, gate: int = 0, prevcnt=N
     x0 = np.zeros(13) if prev_x0 is None else np.asarray(prev_x0, np.float64)
     dev = struct.pack(_DEVSTATE_FMT, int(gate), int(iter) & 0x7FFFFFFF if iter < 2 ** 31 else int(iter) - 2 ** 32,
                       has_prev, int(has_theta), int(U.shape[0] if n_nom is None else n_nom), n_prev, int(gate), 0, 0, 0,
-                      float(theta), float(v_theta), float(c_last), *[float(v) for v in x0], 0.0, 0.0, 0.0, 0.0)
+                      float(theta), float(v_theta), float(c_last), *[float(v) for v in x0], 0.0, 0.0, 0.0, 0.0,
+                      *[float(v) for v in (rotor if rotor is not None else np.zeros(4))], 0.0, 0.0, 0.0, 0.0,
+                      1 if rotor is not None else 0, 0)
     return struct.pack("<4I", 0x4D505049, 1, N_cap, nu) + dev + Uf.tobytes() + pc.tobytes()
 
 

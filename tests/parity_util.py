@@ -56,11 +56,13 @@ def push_oracle_state(gpu, ora) -> None:
     N_cap = gpu.params.N_cap or gpu.params.N
     nu = 5 if gpu.sc.objective == 1 else 4
     prev = ora.prevcnt[: st.n_prev].copy() if st.n_prev else None
-    U = ora.U[: st.n_nom] if st.n_nom else np.tile([gpu.mc.mass * gpu.mc.gravity, 0, 0, 0, 0], (1, 1))
+    rotor = gpu.mc.kind == 1
+    hover_row = [0.0 if rotor else gpu.mc.mass * gpu.mc.gravity, 0, 0, 0, 0]
+    U = ora.U[: st.n_nom] if st.n_nom else np.tile(hover_row, (1, 1))
     blob = mppi.encode_state(N_cap, nu, U, iter=st.iter, gate=st.gate, prevcnt=prev,
                              prev_x0=np.array(st.prev_x0[:]) if st.has_prev else None, theta=st.theta,
                              v_theta=st.v_theta, c_last=st.c_last, has_theta=st.has_theta,
-                             n_nom=st.n_nom)
+                             n_nom=st.n_nom, rotor=ora.rotor if rotor else None)
     gpu.import_state(blob)
 
 
