@@ -120,6 +120,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-closed-loop", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
 
@@ -444,6 +445,16 @@ def main():
         # latency, and device time per solve back to back
         plain["paper_table1_single_solve"] = paper_table1_latency(M, W)
 
+    # ---- closed-loop comparison of the objectives (Sec. V-A protocol) ----
+    closed = None
+    if not args.no_closed_loop and rank == 0:
+        from paper_2509_14726_gb300 import closed_loop as CL
+        tracks = {"circle_4_gates_r5": W.circle_track(4, 5.0), "figure8_8_gates": W.figure8_track(),
+                  "course_7_gates_seed7": W.random_course(7)}
+        closed = {"protocol": "3 laps, 50 Hz, K 4096, N 50; plant = the library's RK4 model; all start 1 m "
+                              "before gate 0 (tracking on its 8 m/s reference); 60 s limit",
+                  "runs": CL.comparison(tracks, laps=3, models=("ctbr", "rotor"), t_max=60.0)}
+
     # ---- serving: a fleet at its own rates, continuous batching vs plain ----
     serving_out = None
     if not args.no_serving and rank == 0:
@@ -480,7 +491,7 @@ def main():
                        "parallelism": f"dp{world} (drones sharded, no collective)"},
             "solves_per_s": len(items) * world / (ms_max / 1e3),
             "gpu_launches": int(launches),
-            "roofline": roofline, "e2e": e2e, "plain": plain, "serving": serving_out,
+            "roofline": roofline, "e2e": e2e, "plain": plain, "serving": serving_out, "closed_loop": closed,
             "tuning": {"block": tuning["block"], "graph_mode": tuning["graph_mode"], "noise_gen": tuning["noise_gen"],
                        "table": tuning["table"]},
             "cpu_baseline": cpu, "clocks": clocks,

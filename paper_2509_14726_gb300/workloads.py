@@ -153,6 +153,26 @@ def circle_gates(n: int = 4, radius: float = 5.0, height: float = 2.0,
     return g
 
 
+def figure8_gates(n: int = 8, a: float = 12.0, height: float = 3.0, size: float = 1.5) -> np.ndarray:
+    """Gates on the lemniscate (a sin t, a sin t cos t) at equal parameter
+    steps, facing along the curve (a stand-in for a figure-8 race track; the
+    crossing at the centre is flown twice per lap)."""
+    g = np.zeros((n, 6))
+    for i in range(n):
+        t = 2.0 * math.pi * (i + 0.5) / n
+        x, y = a * math.sin(t), a * math.sin(t) * math.cos(t)
+        dx, dy = a * math.cos(t), a * math.cos(2.0 * t)
+        g[i] = (x, y, height, math.atan2(dy, dx), 0.5 * size, 0.5 * size)
+    return g
+
+
+def figure8_track(n: int = 8, a: float = 12.0, height: float = 3.0, S: int = 1024) -> Track:
+    key = ("figure8", n, a, height, S)
+    if key not in _TRACK_CACHE:
+        _TRACK_CACHE[key] = build_track(figure8_gates(n, a, height), S)
+    return _TRACK_CACHE[key]
+
+
 def random_gates(seed: int, n: int, box=(30.0, 30.0, 6.0), z_low: float = 1.0,
                  min_spacing: float = 6.0, yaw_jitter_deg: float = 45.0,
                  size: float = 1.5) -> np.ndarray:

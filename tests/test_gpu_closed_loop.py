@@ -83,3 +83,17 @@ def test_c2_tracking_follows_reference(env):
     err = [np.linalg.norm(X[k, :3] - O.ref_eval(tr, k * sc.dt)[:3]) for k in range(0, 1001, 5)]
     rmse = math.sqrt(np.mean(np.square(err)))
     assert rmse < 1.0, f"tracking RMSE {rmse:.3f} m"
+
+
+def test_lap_protocol_on_the_circle(env):
+    """The comparison protocol (Sec. V-A): one lap of the 4-gate circle with
+    each objective, the library's model as the plant.  Every objective
+    completes the lap through the gates, gate progress is the fastest and
+    tracking stays on its reference."""
+    from paper_2509_14726_gb300 import closed_loop as CL
+    out = CL.comparison({"circle": W.circle_track(4, 5.0)}, laps=1, K=2048, N=40, t_max=20.0)
+    g, c, t = (out[f"circle/ctbr/{n}"] for n in ("gate", "contour", "track"))
+    assert g["completed"] and c["completed"] and t["completed"], out
+    assert g["time_s"] < t["time_s"]
+    assert t["tracking_rmse_m"] < 0.2
+    assert all(r["waypoint_error_m"] <= 0.75 * 2 ** 0.5 for r in (g, c, t))
