@@ -439,6 +439,13 @@ __device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int 
 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
 
+// lanes that share one step in the epilogue's weighted sums (power of two <= 32)
+#ifndef MPPI_EPI_LANES
+#define MPPI_EPI_LANES 8
+#endif
+static_assert(MPPI_EPI_LANES >= 1 && MPPI_EPI_LANES <= 32 && (MPPI_EPI_LANES & (MPPI_EPI_LANES - 1)) == 0,
+              "MPPI_EPI_LANES must be a power of two in [1, 32]");
+
 // ROT: rotor-thrust-rate input model (rotor thrusts in the state)
 template <int OBJ, int BF16, int GEN, int ROT>
 __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__ descs,
@@ -856,71 +863,69 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const int NNU = N * kNU;
   const int tile_in_solve = tile.m0 / B;
   double* myP = d.part_P + (size_t)tile_in_solve * NNU;
-  for (int k = wid; k < N; k += nw) {
-    const float* Uk = sU + kNU * k;
+  // each warp takes kEpiRows steps at a time, kEpiLanes lanes per step: a lane
+  // sums every kEpiLanes-th sample of the tile, then the lanes of a step
+  // reduce in a fixed order within their group (log2(kEpiLanes) levels)
+  constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes;
+  const int sub = lane / kEpiLanes, sl = lane % kEpiLanes;
+  for (int k0 = wid * kEpiRows; k0 < N; k0 += nw * kEpiRows) {
+    const int k = k0 + sub;
+    const bool row_ok = k < N;
+    const float* Uk = sU + kNU * (row_ok ? k : 0);
     float hi[kNU], lo[kNU];
     double dacc[kNU];
 #pragma unroll
     for (int j = 0; j < kNU; ++j) { hi[j] = 0.f; lo[j] = 0.f; dacc[j] = 0.0; }
-    for (int i = lane; i < nvalid; i += 32) {
-      const float w = sE[i];
-      float zz[kNU];
-      if (GEN == 2)
-        gen_noise<BF16, false>(d, iter, tile.m0 + i, k, zz, five);
-      else
-        load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + i, zz, five);
+    if (row_ok) {
+      for (int i = sl; i < nvalid; i += kEpiLanes) {
+        const float w = sE[i];
+        float zz[kNU];
+        if (GEN == 2)
+          gen_noise<BF16, false>(d, iter, tile.m0 + i, k, zz, five);
+        else
+          load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + i, zz, five);
 #pragma unroll
-      for (int j = 0; j < kNU; ++j) {
-        if (j >= nu) break;
-        const float u = clampf(Uk[j] + d.sigma[j] * zz[j], d.u_min[j], d.u_max[j]);
-        const float dv = u - Uk[j];
-        if (acc == MPPI_ACC_F64) {
-          dacc[j] = fma((double)w, (double)dv, dacc[j]);
-        } else if (acc == MPPI_ACC_F32) {
-          hi[j] = fmaf(w, dv, hi[j]);
-        } else {
-          kahan_add(hi[j], lo[j], w * dv);
+        for (int j = 0; j < kNU; ++j) {
+          if (j >= nu) break;
+          const float u = clampf(Uk[j] + d.sigma[j] * zz[j], d.u_min[j], d.u_max[j]);
+          const float dv = u - Uk[j];
+          if (acc == MPPI_ACC_F64) {
+            dacc[j] = fma((double)w, (double)dv, dacc[j]);
+          } else if (acc == MPPI_ACC_F32) {
+            hi[j] = fmaf(w, dv, hi[j]);
+          } else {
+            kahan_add(hi[j], lo[j], w * dv);
+          }
         }
       }
     }
-    // cross-lane reduction, fixed order
+    // cross-lane reduction within the step's lane group, fixed order
+    const bool writer = row_ok && sl == 0;
 #pragma unroll
     for (int j = 0; j < kNU; ++j) {
       if (j >= nu) break;
       if (acc == MPPI_ACC_F64) {
         double v = dacc[j];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) myP[kNU * k + j] = v;
+        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (writer) myP[kNU * k + j] = v;
       } else if (acc == MPPI_ACC_F32) {
         float v = hi[j];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) {
-          float2 r = make_float2(v, 0.f);
-          myP[kNU * k + j] = *reinterpret_cast<double*>(&r);
-        }
+        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (writer) myP[kNU * k + j] = pack2(v, 0.f);
       } else {
         float h1 = hi[j], l1 = -lo[j];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
+        for (int o = kEpiLanes / 2; o; o >>= 1) {
           const float h2 = __shfl_xor_sync(0xffffffffu, h1, o), l2 = __shfl_xor_sync(0xffffffffu, l1, o);
-          float s_, e_;
-          two_sum(h1, h2, s_, e_);
-          const float l = e_ + l1 + l2;
-          two_sum(s_, l, h1, l1);
+          add2(h1, l1, h2, l2);
         }
-        if (lane == 0) {
-          float2 r = make_float2(h1, l1);
-          myP[kNU * k + j] = *reinterpret_cast<double*>(&r);
-        }
+        if (writer) myP[kNU * k + j] = pack2(h1, l1);
       }
     }
-    if (lane == 0)
-      for (int j = nu; j < kNU; ++j) {
-        float2 r = make_float2(0.f, 0.f);
-        myP[kNU * k + j] = acc == MPPI_ACC_F64 ? 0.0 : *reinterpret_cast<double*>(&r);
-      }
+    if (writer)
+      for (int j = nu; j < kNU; ++j) myP[kNU * k + j] = acc == MPPI_ACC_F64 ? 0.0 : pack2(0.f, 0.f);
   }
   if (tid == 0) {
     d.part_m[tile_in_solve] = m_t;
