@@ -249,9 +249,16 @@ def start_states(items, t0: float):
     return np.array(X)
 
 
-def cpu_baseline(items, budget_s: float) -> dict:
+def cpu_baseline(items, budget_s: float, M=None, n_parity: int = 6) -> dict:
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    whole solves of the first drones, until the time budget is used."""
+    whole solves of the first drones (binary32-rounded inputs, as the CUDA
+    path receives them), until the time budget is used.  With M (the CUDA
+    binding), the first n_parity sampled drones are also solved once by fresh
+    CUDA handles from the same inputs, and the error against these oracle
+    solves is returned under "parity_vs_oracle": the largest per-sample cost
+    relative error, the largest nominal difference and that difference over
+    its tolerance (1e-5, or 2 * 5e-6 * the oracle's sensitivity where the
+    weights are ill-conditioned)."""
     from oracle import oracle as O
     from paper_2509_14726_gb300 import workloads as W
     O.build()
@@ -259,21 +266,58 @@ def cpu_baseline(items, budget_s: float) -> dict:
     X = start_states(items, t0)
     steps, solves, used = 0, 0, 0.0
     drones = []
+    worst = {"max_rel_J": 0.0, "max_dU": 0.0, "max_dU_over_tol": 0.0, "max_abs_dJ_weighted": 0.0,
+             "max_dU_over_cost_bound": 0.0, "decision_mismatches": 0, "drones": []}
     for i, it in enumerate(items):
-        sc = make_cfg(it)
-        ctl = O.OracleController(W.ModelConfig(), sc, it.track)
+        mc, sc, tr = W.f32_model(W.ModelConfig()), W.f32_solve(make_cfg(it)), it.track.as_f32()
+        x = np.float32(X[i]).astype(np.float64)
+        ctl = O.OracleController(mc, sc, tr)
         t = time.perf_counter()
-        ctl.solve(X[i], t0)
+        r = ctl.solve(x, t0)
         used += time.perf_counter() - t
         steps += it.K * it.N
         solves += 1
         drones.append(i)
-        if used >= budget_s:
+        if M is not None and i < n_parity:
+            gpu = M.Controller(mc, sc, tr)
+            gpu.solve(x, t0)
+            J = gpu.costs()
+            ok = r["near_flag"] == 0
+            denom = np.maximum(np.abs(r["J"]), r["Jabs"])
+            rel = np.abs(J - r["J"]) / np.where(denom > 0, denom, 1.0)
+            nu = 5 if it.objective == 1 else 4
+            dU = np.abs(gpu.unew()[:, :nu] - r["Unew"][:, :nu])
+            tol = np.maximum(1e-5, 2 * 5e-6 * r["sens"][:, :nu])
+            # the nominal error explained by the measured cost errors of the
+            # weighted samples (Eq. 4 / 5: dU <= 2 max|dJ| (1/lambda) sum w |u - U|)
+            wsig = ok & (r["w"] > 1e-8)
+            dJw = float(np.max(np.abs(J - r["J"])[wsig])) if wsig.any() else 0.0
+            bound = np.maximum(1e-5, 2 * dJw * r["sens"][:, :nu])
+            npass, first = gpu.sample_info()
+            if it.objective == 0:
+                worst["decision_mismatches"] += int(((npass != r["npass"]) | (first != r["first_pass"])).sum())
+            worst["max_rel_J"] = max(worst["max_rel_J"], float(rel[ok].max()))
+            worst["max_dU"] = max(worst["max_dU"], float(dU.max()))
+            worst["max_dU_over_tol"] = max(worst["max_dU_over_tol"], float((dU / tol).max()))
+            worst["max_abs_dJ_weighted"] = max(worst["max_abs_dJ_weighted"], dJw)
+            worst["max_dU_over_cost_bound"] = max(worst["max_dU_over_cost_bound"], float((dU / bound).max()))
+            worst.setdefault("per_drone", []).append(
+                {"drone": i, "objective": it.objective, "K": it.K, "N": it.N, "max_rel_J": float(rel[ok].max()),
+                 "dJw": dJw, "max_dU": float(dU.max()), "dU_over_tol": float((dU / tol).max()),
+                 "flagged": int((~ok).sum())})
+            worst["drones"].append(i)
+            gpu.close()
+        if used >= budget_s and i + 1 >= (n_parity if M is not None else 1):
             break
-    return {"value": steps / used, "unit": "rollout-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{solves} whole solves (drones {drones[0]}..{drones[-1]} of the batch workload, "
-                      f"{steps} rollout steps, {used:.1f} s, single thread)",
-            "solves_per_s": solves / used}
+    out = {"value": steps / used, "unit": "rollout-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{solves} whole solves (drones {drones[0]}..{drones[-1]} of the batch workload, "
+                     f"{steps} rollout steps, {used:.1f} s, single thread)",
+           "solves_per_s": solves / used}
+    if M is not None:
+        worst["tolerances"] = ("J relative 1e-4; nominal 1e-5 or 2*5e-6*sensitivity (fixed cost-error model), "
+                               "and 1e-5 or 2*max|dJ of weighted samples|*sensitivity (measured cost errors)")
+        out["parity_vs_oracle"] = worst
+    return out
 
 
 def run_reference(args, world, rank):
@@ -475,8 +519,10 @@ def main():
                                          "plain": SV.run_plain(sub, sched_lo, time_limit_s=4.0)}}
 
     cpu = None
+    parity = None
     if rank == 0:
-        cpu = cpu_baseline(items, args.cpu_sample_s)
+        cpu = cpu_baseline(items, args.cpu_sample_s, M)
+        parity = cpu.pop("parity_vs_oracle")
 
     if rank == 0:
         line = {
@@ -494,7 +540,7 @@ def main():
             "roofline": roofline, "e2e": e2e, "plain": plain, "serving": serving_out, "closed_loop": closed,
             "tuning": {"block": tuning["block"], "graph_mode": tuning["graph_mode"], "noise_gen": tuning["noise_gen"],
                        "table": tuning["table"]},
-            "cpu_baseline": cpu, "clocks": clocks,
+            "cpu_baseline": cpu, "parity_vs_oracle": parity, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     M.mppi_batch_destroy(plan)

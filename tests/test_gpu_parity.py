@@ -449,3 +449,40 @@ def test_batch_mixing_variants_equals_alone(M, use_graph):
     for g1, g2, _ in pairs:
         g1.close()
         g2.close()
+
+
+def test_full_bench_batch_sampled_against_oracle(O, M):
+    """The bench's own workload and launch: the 256-drone uneven batch (K
+    log-uniform in [1024, 16384], N in [20, 80], 1/3 each objective), solved
+    once through a captured batch plan with concurrent branches.  Sampled
+    solves -- the first two of each objective, the largest K and the longest
+    N -- against the oracle on the same inputs.  The nominal tolerance takes
+    the measured cost error of the weighted samples (long horizons and large
+    tracking costs carry a larger absolute binary32 error)."""
+    items = W.c3_batch(n_drones=256, seed=3)
+    t0 = 0.3
+    cases, ctls, X0 = [], [], []
+    for it in items:
+        sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, lam=1.0, seed=0, drone_id=it.drone_id)
+        x = it.x0.copy()
+        if it.objective == 2:
+            x = it.track.ref[int(round(t0 / it.track.dt_ref)) % it.track.ref.shape[0]].copy()
+        case = f32_case(W.ModelConfig(), sc, it.track, x)
+        cases.append(case)
+        ctls.append(M.Controller(case.mc, case.sc, case.tr))
+        X0.append(case.x0)
+    plan = M.mppi_batch_create([c.h for c in ctls], use_graph=1)
+    M.mppi_batch_solve(plan, len(items), np.array(X0), np.full(len(items), t0))
+    picked = []
+    for obj in (0, 1, 2):
+        picked += [i for i, it in enumerate(items) if it.objective == obj][:2]
+    picked += [int(np.argmax([it.K for it in items])), int(np.argmax([it.N for it in items]))]
+    for i in dict.fromkeys(picked):
+        c = cases[i]
+        r = O.OracleController(c.mc, c.sc, c.tr).solve(c.x0, t0)
+        st = compare(ctls[i], r, f"bench drone {i} (objective {c.sc.objective}, K {c.sc.K}, N {c.sc.N})",
+                     measured_cost_bound=True)
+        print(f"\nbench drone {i}: {st}")
+    M.mppi_batch_destroy(plan)
+    for c in ctls:
+        c.close()
