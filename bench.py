@@ -42,6 +42,9 @@ sys.path.insert(0, ROOT)
 # compare = 1, rsqrt = 1): sampling, RK4, objective, penalty and cost sum,
 # counted from the kernel's arithmetic; the derivation is in the design doc
 FLOPS_PER_STEP = {0: 423.0, 1: 491.0, 2: 478.0}
+# the same for the rotor-thrust-rate model: its RK4 step counts 466 against 358
+# (saturating compensated thrust ramps, three sets of rotor forces and torques)
+FLOPS_PER_STEP_ROTOR = {0: 531.0, 1: 599.0, 2: 586.0}
 
 
 def measured_traffic(steps_by_objective):
@@ -121,6 +124,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-closed-loop", action="store_true")
+    ap.add_argument("--no-rotor", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     return ap.parse_args()
 
@@ -451,6 +455,35 @@ def main():
     noise_bytes = sum(it.K * it.N * (16 + (4 if it.objective == 1 else 0)) for it in items)
     roofline["noise_kernel_gbs"] = noise_bytes / (float(prof[0]) / 1e3) / 1e9 if prof[0] > 0 else None
 
+    # ---- the same batch with the rotor-thrust-rate model (Eq. 2 as printed) ----
+    rotor_out = None
+    if rank == 0 and not args.no_rotor:
+        rctl = [M.Controller(W.rotor_model(), W.rotor_solve(make_cfg(it)), it.track) for it in items]
+        rplan = M.mppi_batch_create([c.h for c in rctl], use_graph=1)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                M.mppi_batch_solve_async(rplan, d_x0.data_ptr(), d_t0.data_ptr(), stream, d_u0.data_ptr())
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            for _ in range(10):
+                M.mppi_batch_solve_async(rplan, d_x0.data_ptr(), d_t0.data_ptr(), stream, d_u0.data_ptr())
+            r1.record(stream)
+        stream.synchronize()
+        rms = r0.elapsed_time(r1) / 10
+        M.mppi_batch_solve(rplan, len(items), np.float32(X0), np.full(len(items), t0))  # host inputs of the plan
+        rprof = M.mppi_batch_profile(rplan, 5, stream)
+        rroll_ms = float(rprof[1] + rprof[2] + rprof[3])
+        rflops = sum(it.K * it.N * FLOPS_PER_STEP_ROTOR[it.objective] for it in items)
+        rotor_out = {"value": steps_per_solve / (rms / 1e3), "unit": "rollout-steps/s", "ms_per_step": rms,
+                     "phase_ms": {"noise": float(rprof[0]), "rollout_gate": float(rprof[1]),
+                                  "rollout_contour": float(rprof[2]), "rollout_track": float(rprof[3]),
+                                  "nominal": float(rprof[4])},
+                     "roofline": {"bound": "alu", "achieved": rflops / (rroll_ms / 1e3) / 1e12, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": rflops / (rroll_ms / 1e3) / 1e12 / peak}}
+        M.mppi_batch_destroy(rplan)
+        for c in rctl:
+            c.close()
+
     # ---- plain path: one solve per launch sequence ----
     plain = None
     if not args.no_plain and rank == 0:
@@ -537,7 +570,8 @@ def main():
                        "parallelism": f"dp{world} (drones sharded, no collective)"},
             "solves_per_s": len(items) * world / (ms_max / 1e3),
             "gpu_launches": int(launches),
-            "roofline": roofline, "e2e": e2e, "plain": plain, "serving": serving_out, "closed_loop": closed,
+            "roofline": roofline, "e2e": e2e, "rotor_model_batch": rotor_out, "plain": plain,
+            "serving": serving_out, "closed_loop": closed,
             "tuning": {"block": tuning["block"], "graph_mode": tuning["graph_mode"], "noise_gen": tuning["noise_gen"],
                        "table": tuning["table"]},
             "cpu_baseline": cpu, "parity_vs_oracle": parity, "clocks": clocks,
