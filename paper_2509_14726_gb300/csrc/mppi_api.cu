@@ -131,6 +131,10 @@ struct mppi_batch_s {
   std::vector<mppi_handle> hs;
   std::vector<unsigned> versions;
   int n = 0;
+  // mppi_solve_batch's cache (guarded by g_plan_mu): calls running this plan,
+  // and whether it has left the cache (the last user then destroys it)
+  int users = 0;
+  bool evicted = false;
   SolveDesc* d_descs = nullptr;
   struct Group {
     int objective, bf16, block, gen, nom, rot;  // gen: MPPI_NOISEGEN_*; nom: nominal candidate; rot: rotor model
@@ -547,8 +551,11 @@ int mppi_destroy(mppi_handle h) {
     for (size_t i = 0; i < g_plans.size();) {
       mppi_batch p = g_plans[i];
       if (std::find(p->hs.begin(), p->hs.end(), h) != p->hs.end()) {
-        mppi_batch_destroy(p);
         g_plans.erase(g_plans.begin() + i);
+        if (p->users == 0)
+          mppi_batch_destroy(p);
+        else
+          p->evicted = true;
       } else {
         ++i;
       }
@@ -1206,6 +1213,15 @@ int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const d
                      float* u0s_out) {
   if (n < 1 || !hs || !x0s || !u0s_out) return fail(MPPI_ERR_ARG, "bad arguments");
   mppi_batch plan = nullptr;
+  // a plan leaves the cache when it goes stale, when the cache is full or
+  // when one of its handles is destroyed; one that a call is running is only
+  // marked, and its last user destroys it
+  auto drop = [](mppi_batch p) {
+    if (p->users == 0)
+      mppi_batch_destroy(p);
+    else
+      p->evicted = true;
+  };
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     for (size_t i = 0; i < g_plans.size(); ++i) {
@@ -1216,8 +1232,8 @@ int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const d
       if (fresh) {
         plan = p;
       } else {
-        mppi_batch_destroy(p);
         g_plans.erase(g_plans.begin() + i);
+        drop(p);
       }
       break;
     }
@@ -1225,13 +1241,20 @@ int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const d
       int rc = mppi_batch_create(n, hs, 1, &plan);
       if (rc) return rc;
       if (g_plans.size() >= 8) {
-        mppi_batch_destroy(g_plans.front());
+        mppi_batch old = g_plans.front();
         g_plans.erase(g_plans.begin());
+        drop(old);
       }
       g_plans.push_back(plan);
     }
+    ++plan->users;
   }
-  return mppi_batch_solve(plan, x0s, t0s, stream, u0s_out);
+  const int rc = mppi_batch_solve(plan, x0s, t0s, stream, u0s_out);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (--plan->users == 0 && plan->evicted) mppi_batch_destroy(plan);
+  }
+  return rc;
 }
 
 }  // extern "C"

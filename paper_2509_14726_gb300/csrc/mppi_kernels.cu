@@ -14,6 +14,7 @@
 //   nominal_kernel   rollout of U*_new from x0 with the gate logic: the gate
 //                    pass counts that the temporal-consistency rule of the next
 //                    solve reads (Sec. IV-A).
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 
@@ -1205,8 +1206,8 @@ __global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, int rotor, float
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-static unsigned long long g_launches = 0;
-unsigned long long launches_so_far() { return g_launches; }
+static std::atomic<unsigned long long> g_launches{0};  // host threads may launch concurrently
+unsigned long long launches_so_far() { return g_launches.load(); }
 void add_launches(int n) { g_launches += (unsigned long long)n; }
 
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,

@@ -163,59 +163,11 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   char* b = static_cast<char*>(base);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // descriptor (the same fields mppi_create derives), pointing into the scratch
+  // descriptor (the model and weight fields that mppi_create derives, from
+  // the same routine), pointing into the scratch
   SolveDesc d;
   memset(&d, 0, sizeof d);
-  d.mass = m.mass;
-  d.inv_mass = (float)(1.0 / (double)m.mass);
-  d.gravity = m.gravity;
-  d.k_omega = m.k_omega;
-  const double Jx = m.inertia[0], Jy = m.inertia[1], Jz = m.inertia[2];
-  d.gyro[0] = (float)((Jz - Jy) / Jx);
-  d.gyro[1] = (float)((Jx - Jz) / Jy);
-  d.gyro[2] = (float)((Jy - Jx) / Jz);
-  for (int i = 0; i < 3; ++i) d.drag[i] = m.drag[i];
-  d.has_drag = (m.drag[0] != 0.f || m.drag[1] != 0.f || m.drag[2] != 0.f) ? 1 : 0;
-  for (int i = 0; i < kNU; ++i) {
-    d.u_min[i] = m.u_min[i];
-    d.u_max[i] = m.u_max[i];
-    d.sigma[i] = p.sigma[i];
-  }
-  d.omega_max = m.omega_max;
-  d.z_floor = m.z_floor;
-  d.objective = p.objective;
-  d.K = p.K;
-  d.N = p.N;
-  d.nu = five ? 5 : 4;
-  d.dt = p.dt;
-  d.lambda = p.lambda;
-  d.inv_lambda = (float)(1.0 / (double)p.lambda);
-  d.seed = p.seed;
-  d.drone_id = p.drone_id;
-  d.noise_bf16 = bf16;
-  d.noise_gen = p.noise_gen;
-  d.nominal_sample = p.nominal_sample ? 1 : 0;
-  d.warm_keep = p.warm_start == MPPI_WARM_KEEP ? 1 : 0;
-  d.accum = p.accum;
-  d.w_limit = p.w_limit;
-  d.q_near = p.q_near;
-  d.r_near2 = p.r_near * p.r_near;
-  d.temporal_rule = p.temporal_rule;
-  d.q_lag = p.q_lag;
-  d.q_cont = p.q_cont;
-  for (int i = 0; i < 3; ++i) d.q_omega[i] = p.q_omega[i];
-  d.r_dv = p.r_dv;
-  d.r_dthrust = p.r_dthrust;
-  d.mu = p.mu;
-  d.v_theta_max = p.v_theta_max;
-  d.theta_back = p.theta_back;
-  d.theta_ahead = p.theta_ahead;
-  for (int i = 0; i < kNX; ++i) {
-    d.Q[i] = p.Q[i];
-    d.QN[i] = p.QN[i];
-  }
-  for (int i = 0; i < 4; ++i) d.R[i] = p.R[i];
-  d.hover = m.mass * m.gravity;
+  fill_model_params(m, p, five ? 5 : 4, d);
   d.gates = d_track->gates;
   d.n_gates = d_track->n_gates;
   d.closed = d_track->closed ? 1 : 0;

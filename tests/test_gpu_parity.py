@@ -486,3 +486,47 @@ def test_full_bench_batch_sampled_against_oracle(O, M):
     M.mppi_batch_destroy(plan)
     for c in ctls:
         c.close()
+
+
+def test_solve_batch_cache_under_threads(M):
+    """mppi_solve_batch from several threads at once, with more distinct
+    handle sets than its plan cache holds, so that plans leave the cache
+    while other calls run them: every result equals the same solves made
+    one handle at a time."""
+    import threading
+    items = W.c3_batch(n_drones=24, K_lo=256, K_hi=1024, N_lo=5, N_hi=15)
+    errors = []
+
+    def worker(tid):
+        try:
+            sets = []
+            for s in range(3):
+                its = items[tid * 6 + 2 * s: tid * 6 + 2 * s + 2]
+                pair = []
+                for it in its:
+                    sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id)
+                    case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
+                    pair.append((M.Controller(case.mc, case.sc, case.tr), M.Controller(case.mc, case.sc, case.tr),
+                                 case))
+                sets.append(pair)
+            for rep in range(4):
+                for pair in sets:
+                    X0 = np.array([c.x0 for _, _, c in pair])
+                    ub, _ = M.mppi_solve_batch([g.h for g, _, _ in pair], X0, np.full(len(pair), 0.1 * rep))
+                    for i, (_, alone, c) in enumerate(pair):
+                        ua, _ = alone.solve(c.x0, 0.1 * rep)
+                        if not np.array_equal(ub[i], ua):
+                            errors.append((tid, rep, i, ub[i], ua))
+            for pair in sets:
+                for g, alone, _ in pair:
+                    g.close()
+                    alone.close()
+        except Exception as e:  # reported below
+            errors.append((tid, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors[:3]
