@@ -544,10 +544,16 @@ def main():
         sub = fleet[:200]
         sched_lo = SV.make_schedule(sub, duration_s=2.0, time_scale=0.1, K_choices=[1024, 4096, 16384],
                                     N_choices=[30, 50, 80], seed=0)
+        # the full fleet rate (2.35e5 requests/s offered, more than one GPU
+        # serves): the achieved rate under overload is the server's capacity
+        sched_full = SV.make_schedule(fleet, duration_s=1.0, time_scale=1.0, K_choices=[1024, 4096, 16384],
+                                      N_choices=[30, 50, 80], seed=1)
+        saturated = SV.run_served(fleet, sched_full, budget_bytes=40 << 30, n_slots=3, max_batch=512)
         serving_out = {
             "fleet": "2000 drones at 50/100/200 Hz x 0.3 (Poisson-jittered), K in {1024,4096,16384}, "
                      "N in {30,50,80}, 5-9 gate courses, 40 GB scratch budget, 2 s",
             "served": served, "plain_one_solve_per_request": plain_s,
+            "overload_full_rate_1s": saturated,
             "low_load_200_drones_x0.1": {"served": SV.run_served(sub, sched_lo),
                                          "plain": SV.run_plain(sub, sched_lo, time_limit_s=4.0)}}
 
