@@ -369,18 +369,18 @@ def main():
     X0 = start_states(items, t0)
     from paper_2509_14726_gb300 import workloads as W
     # ---- autotuning (untimed): block size and graph form of the batch plan ----
-    tuning = {"block": 128, "graph_mode": 1, "noise_gen": M.NOISEGEN_DEFAULT, "table": None}
+    tuning = {"block": 128, "graph_mode": 1, "noise_gen": M.NOISEGEN_DEFAULT, "spt": 1, "table": None}
     if not args.no_tune:
         from paper_2509_14726_gb300 import autotune as AT
 
-        def make_handles(block, noise_gen=None):
-            return [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=block, noise_gen=noise_gen)
+        def make_handles(block, noise_gen=None, spt=1):
+            return [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=block, noise_gen=noise_gen, spt=spt)
                     for it in items]
 
         tuning = AT.tune_batch(make_handles, X0, t0, blocks=(64, 96, 128), modes=(1, 2), cache=None,
-                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN))
-    ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=tuning["block"], noise_gen=tuning["noise_gen"])
-            for it in items]
+                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN), spts=(1, 2))
+    ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=tuning["block"], noise_gen=tuning["noise_gen"],
+                         spt=tuning["spt"]) for it in items]
     hs = [c.h for c in ctls]
     steps_per_solve = float(sum(it.K * it.N for it in items))
     flops = {o: sum(it.K * it.N * FLOPS_PER_STEP[o] for it in items if it.objective == o) for o in (0, 1, 2)}
@@ -579,6 +579,7 @@ def main():
             "roofline": roofline, "e2e": e2e, "rotor_model_batch": rotor_out, "plain": plain,
             "serving": serving_out, "closed_loop": closed,
             "tuning": {"block": tuning["block"], "graph_mode": tuning["graph_mode"], "noise_gen": tuning["noise_gen"],
+                       "spt": tuning["spt"],
                        "table": tuning["table"]},
             "cpu_baseline": cpu, "parity_vs_oracle": parity, "clocks": clocks,
         }

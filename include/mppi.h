@@ -78,6 +78,7 @@ enum { MPPI_WARM_SHIFT = 0, MPPI_WARM_KEEP = 1 };
 #define MPPI_NU 5
 #define MPPI_MAX_N 128     /* longest horizon a handle may use */
 #define MPPI_MAX_GATES 64  /* most gates a track may have */
+#define MPPI_MAX_SPT 8     /* most samples one rollout thread may run */
 
 /* Quadrotor model (Eq. 2).  kind selects the input parameterisation:
  *   MPPI_MODEL_CTBR: u = (collective thrust, body-rate command); body-rate
@@ -137,6 +138,10 @@ typedef struct {
   int32_t noise_gen;     /* MPPI_NOISEGEN_* */
   int32_t nominal_sample; /* 1: sample 0 is the unperturbed nominal (Eq. 3 with du = 0) */
   int32_t warm_start;    /* MPPI_WARM_* */
+  int32_t samples_per_thread; /* rollouts one thread runs one after another, 1..8 (0 = 1):
+                                 a block covers block x samples_per_thread samples, so a
+                                 solve launches fewer blocks and pays the per-block setup
+                                 (nominal copy, reductions, merge) fewer times */
 } mppi_params_t;
 
 /* Track: waypoints W, arc-length path P_arc and reference tau_ref

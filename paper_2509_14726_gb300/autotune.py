@@ -10,6 +10,8 @@ the launching stream) over the knobs the kernels expose:
 * where the normals are drawn: a separate Philox pass, inside the rollout
   (stored), or inside the rollout and again in the update (never stored:
   no noise memory); the same draws in every form;
+* samples per thread (a block covers block x spt samples, fewer blocks per
+  solve), searched on the best of the knobs above;
 * optionally the noise storage (float32 or bfloat16; bfloat16 changes the
   numerics, so it is only searched when the caller allows it).
 
@@ -122,10 +124,15 @@ def tune_single(mc, sc, track, blocks: Sequence[int] = BLOCKS, allow_bf16: bool 
 
 
 def time_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float, mode: int, block: int,
-               reps: int = 10, warmup: int = 3, noise_gen: Optional[int] = None) -> float:
+               reps: int = 10, warmup: int = 3, noise_gen: Optional[int] = None, spt: int = 1) -> float:
     """Mean device time (ms) of one batched solve (mppi_batch_solve_async)."""
     torch = _torch()
-    ctls = make_handles(block) if noise_gen is None else make_handles(block, noise_gen=noise_gen)
+    kw = {}
+    if noise_gen is not None:
+        kw["noise_gen"] = noise_gen
+    if spt != 1:
+        kw["spt"] = spt
+    ctls = make_handles(block, **kw)
     plan = M.mppi_batch_create([c.h for c in ctls], use_graph=mode)
     n = len(ctls)
     s = torch.cuda.Stream()
@@ -150,10 +157,13 @@ def time_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float, mo
 
 def tune_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float,
                blocks: Sequence[int] = BLOCKS, modes: Sequence[int] = (1, 2), cache: Optional[Cache] = None,
-               key: Optional[str] = None, noise_gens: Optional[Sequence[int]] = None) -> dict:
-    """Best (block, graph form[, noise generation]) for a batch;
-    make_handles(block) builds the batch's Controllers with that block size
-    (make_handles(block, noise_gen=g) when noise_gens is given)."""
+               key: Optional[str] = None, noise_gens: Optional[Sequence[int]] = None,
+               spts: Sequence[int] = (1,)) -> dict:
+    """Best (block, graph form[, noise generation][, samples per thread])
+    for a batch; make_handles(block) builds the batch's Controllers with that
+    block size (make_handles(block, noise_gen=g) when noise_gens is given,
+    make_handles(block, ..., spt=s) for the samples-per-thread stage).  The
+    samples per thread are searched on the best configuration of the others."""
     full_key = f"{gpu_name()}|batch|{key}" if key else None
     if cache is not None and full_key and cache.get(full_key):
         return cache.get(full_key)
@@ -163,10 +173,18 @@ def tune_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float,
         for b in blocks:
             for m in modes:
                 table.append({"block": b, "graph_mode": m, "noise_gen": M.NOISEGEN_DEFAULT if g is None else g,
-                              "ms": time_batch(make_handles, x0s, t0, m, b, noise_gen=g)})
+                              "spt": 1, "ms": time_batch(make_handles, x0s, t0, m, b, noise_gen=g)})
+    best = min(table, key=lambda r: r["ms"])
+    for s in spts:
+        if s == 1:
+            continue
+        g = None if noise_gens is None else best["noise_gen"]
+        table.append({"block": best["block"], "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
+                      "spt": s, "ms": time_batch(make_handles, x0s, t0, best["graph_mode"], best["block"],
+                                                 noise_gen=g, spt=s)})
     best = min(table, key=lambda r: r["ms"])
     out = {"block": best["block"], "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
-           "ms": best["ms"], "table": table}
+           "spt": best["spt"], "ms": best["ms"], "table": table}
     if cache is not None and full_key:
         cache.put(full_key, out)
     return out

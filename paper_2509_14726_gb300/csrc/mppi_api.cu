@@ -203,6 +203,8 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   int blk = p->block ? p->block : 128;
   if (blk < 32 || blk > rollout_max_block() || blk % 32)
     return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
+  if (p->samples_per_thread < 0 || p->samples_per_thread > MPPI_MAX_SPT)
+    return fail(MPPI_ERR_ARG, "samples_per_thread %d outside [0, %d]", p->samples_per_thread, MPPI_MAX_SPT);
   if (t->n_gates < 0 || t->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p->objective == MPPI_OBJ_GATE && (t->n_gates < 1 || !t->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs at least one gate");
@@ -286,6 +288,7 @@ void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int 
   d.noise_gen = p.noise_gen;
   d.nominal_sample = p.nominal_sample ? 1 : 0;
   d.warm_keep = p.warm_start == MPPI_WARM_KEEP ? 1 : 0;
+  d.spt = p.samples_per_thread > 0 ? p.samples_per_thread : 1;
   d.accum = p.accum;
   d.w_limit = p.w_limit;
   d.q_near = p.q_near;
@@ -321,14 +324,14 @@ void fill_desc(mppi_handle h) {
   SolveDesc& d = h->hd;
   d.N_cap = h->N_cap;
   d.block = h->block;
-  d.n_tiles = (h->params.K + h->block - 1) / h->block;
+  d.n_tiles = (h->params.K + tile_samples(d) - 1) / tile_samples(d);
   d.ext_noise = 0;
 }
 
 int upload_tiles(mppi_handle h) {
   const int T = h->hd.n_tiles;
   std::vector<Tile> tl(T);
-  for (int i = 0; i < T; ++i) tl[i] = Tile{0, i * h->block};
+  for (int i = 0; i < T; ++i) tl[i] = Tile{0, i * tile_samples(h->hd)};
   CU(cudaMemcpy(h->d_tiles, tl.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice));
   return MPPI_OK;
 }
@@ -419,6 +422,7 @@ int mppi_default_params(mppi_params_t* p, int32_t objective, int32_t K, int32_t 
   p->noise_dtype = MPPI_NOISE_F32;
   p->accum = MPPI_ACC_KAHAN32;
   p->block = 128;
+  p->samples_per_thread = 1;
   return MPPI_OK;
 }
 
@@ -583,7 +587,7 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
   h->params.N = N;
   h->hd.K = K;
   h->hd.N = N;
-  h->hd.n_tiles = (K + h->block - 1) / h->block;
+  h->hd.n_tiles = (K + tile_samples(h->hd) - 1) / tile_samples(h->hd);
   CU(cudaMemcpy(h->d_desc, &h->hd, sizeof h->hd, cudaMemcpyHostToDevice));
   int rc = upload_tiles(h);
   if (rc) return rc;
@@ -601,7 +605,7 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   } else {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
   }
-  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, h->block, merge_cap(d.n_tiles));
+  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles));
   CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen,
                     d.rotor));
   return MPPI_OK;
@@ -975,11 +979,12 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     };
     int gi = find(rg, k);
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
-    rsmem[gi] = std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, d.block, merge_cap(d.n_tiles)));
+    rsmem[gi] =
+        std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles)));
     const int gn = d.noise_gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
-      rg[gi].second.push_back(Tile{i, t * d.block});
-      if (gn >= 0) ng[gn].second.push_back(Tile{i, t * d.block});
+      rg[gi].second.push_back(Tile{i, t * tile_samples(d)});
+      if (gn >= 0) ng[gn].second.push_back(Tile{i, t * tile_samples(d)});
     }
     if (d.objective == MPPI_OBJ_GATE) which.push_back(i);
   }

@@ -104,7 +104,11 @@ struct SolveDesc {
   // rotor-thrust-rate model (model kind MPPI_MODEL_ROTOR_RATE)
   int32_t rotor;
   float arm2, c_tau, thrust_min, thrust_max, inv_J[3];
+  int32_t spt;          // samples per thread: a tile holds block x spt samples
 };
+
+// samples one rollout block covers
+__host__ __device__ inline int tile_samples(const SolveDesc& d) { return d.block * d.spt; }
 
 // device-side per-launch inputs and outputs (indexed by the solve's position
 // in the batch); pointers may be device or mapped host memory

@@ -185,12 +185,13 @@ __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
 // shared-memory layout of the rollout kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_merge, total;
+  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_j, off_merge, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, int block, int merge_cap,
+// tile: samples per tile (threads per block x samples per thread)
+__host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, int tile, int merge_cap,
                                                   int path_in_smem) {
   SmemLayout L;
   uint32_t o = 0;
@@ -205,7 +206,9 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
   L.off_xref = o;
   if (objective == MPPI_OBJ_TRACK) o += align16((uint32_t)(N + 1) * kNX * 4u);
   L.off_e = o;
-  o += align16((uint32_t)block * 4u);
+  o += align16((uint32_t)tile * 4u);
+  L.off_j = o;  // the tile's costs as compensated pairs: [tile] hi, then [tile] lo
+  o += align16((uint32_t)tile * 8u);
   L.off_merge = o;
   o += align16((uint32_t)merge_cap * 8u);
   L.total = o;
@@ -214,8 +217,8 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
 
 __host__ __device__ int path_fits_smem(int S) { return S > 0 && S * 24 <= 96 * 1024; }
 
-uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap) {
-  return smem_layout(N, objective, S, block, merge_cap, path_fits_smem(S)).total;
+uint32_t rollout_smem_bytes(int N, int objective, int S, int tile, int merge_cap) {
+  return smem_layout(N, objective, S, tile, merge_cap, path_fits_smem(S)).total;
 }
 
 // ---------------------------------------------------------------------------
@@ -229,45 +232,49 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
   const Tile tile = tiles[blockIdx.x];
   const SolveDesc& d = descs[tile.solve];
   const int K = d.K, N = d.N;
-  const int m = tile.m0 + threadIdx.x;
-  if (d.ext_noise || m >= K || threadIdx.x >= d.block) return;
+  if (d.ext_noise || threadIdx.x >= d.block) return;
   const uint32_t iter = d.st->iter;
   const bool five = d.nu == 5;
-  if (NOM && m == 0 && d.nominal_sample) {
-    // the nominal candidate (Eq. 3 with du = 0) is stored as zero normals
-    for (int k = 0; k < N; ++k) {
-      const size_t idx = (size_t)k * K;
-      if (BF16) {
-        d.Zb[idx] = make_uint2(0u, 0u);
-        if (five) d.Z5b[idx] = __float2bfloat16_rn(0.f);
-      } else {
-        d.Z4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (five) d.Z5[idx] = 0.f;
+  // the thread's samples: m0 + tid + r block, r < samples per thread
+  for (int r = 0; r < d.spt; ++r) {
+    const int m = tile.m0 + threadIdx.x + r * d.block;
+    if (m >= K) return;
+    if (NOM && m == 0 && d.nominal_sample) {
+      // the nominal candidate (Eq. 3 with du = 0) is stored as zero normals
+      for (int k = 0; k < N; ++k) {
+        const size_t idx = (size_t)k * K;
+        if (BF16) {
+          d.Zb[idx] = make_uint2(0u, 0u);
+          if (five) d.Z5b[idx] = __float2bfloat16_rn(0.f);
+        } else {
+          d.Z4[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (five) d.Z5[idx] = 0.f;
+        }
       }
+      continue;
     }
-    return;
-  }
 #pragma unroll kNoiseUnroll
-  for (int k = 0; k < N; ++k) {
-    const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
-    const size_t idx = (size_t)k * K + m;
-    if (BF16) {
-      __nv_bfloat162 a = __floats2bfloat162_rn(z.x, z.y), b = __floats2bfloat162_rn(z.z, z.w);
-      uint2 w;
-      w.x = *reinterpret_cast<uint32_t*>(&a);
-      w.y = *reinterpret_cast<uint32_t*>(&b);
-      d.Zb[idx] = w;
-    } else {
-      d.Z4[idx] = z;
-    }
-    if (five) {
-      // the 5th normal is the first output of block 1 (one Box-Muller pair)
-      const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
-      const float z5 = box_muller(x5.x, x5.y).x;
-      if (BF16)
-        d.Z5b[idx] = __float2bfloat16_rn(z5);
-      else
-        d.Z5[idx] = z5;
+    for (int k = 0; k < N; ++k) {
+      const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
+      const size_t idx = (size_t)k * K + m;
+      if (BF16) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(z.x, z.y), b = __floats2bfloat162_rn(z.z, z.w);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&a);
+        w.y = *reinterpret_cast<uint32_t*>(&b);
+        d.Zb[idx] = w;
+      } else {
+        d.Z4[idx] = z;
+      }
+      if (five) {
+        // the 5th normal is the first output of block 1 (one Box-Muller pair)
+        const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
+        const float z5 = box_muller(x5.x, x5.y).x;
+        if (BF16)
+          d.Z5b[idx] = __float2bfloat16_rn(z5);
+        else
+          d.Z5[idx] = z5;
+      }
     }
   }
 }
@@ -476,13 +483,16 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const SolveDesc& d = sd;
   const int K = d.K, N = d.N, nu = d.nu, B = d.block;
   const int path_smem = path_fits_smem(d.S);
-  const SmemLayout Ls = smem_layout(N, OBJ, d.S, B, max(d.n_tiles, 32), path_smem);
+  // the tile: TS = B spt samples; thread tid runs m0 + tid + rep B, rep < spt
+  const int spt = d.spt, TS = B * spt;
+  const SmemLayout Ls = smem_layout(N, OBJ, d.S, TS, max(d.n_tiles, 32), path_smem);
   float* sU = reinterpret_cast<float*>(smem + Ls.off_U);
   int* sPrev = reinterpret_cast<int*>(smem + Ls.off_prev);
   GateF* sG = reinterpret_cast<GateF*>(smem + Ls.off_gates);
   float* sPath = path_smem ? reinterpret_cast<float*>(smem + Ls.off_path) : nullptr;
   float* sX = reinterpret_cast<float*>(smem + Ls.off_xref);
   float* sE = reinterpret_cast<float*>(smem + Ls.off_e);
+  float* sJ = reinterpret_cast<float*>(smem + Ls.off_j);  // [TS] hi (NaN: not valid), [TS] lo
   double* sMerge = reinterpret_cast<double*>(smem + Ls.off_merge);
   const float* path = path_smem ? sPath : d.path;
 
@@ -615,9 +625,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     for (int i = tid; i < (N + 1) * kNX; i += blockDim.x) d.xref[i] = sX[i];
   }
 
-  // ---- the rollout: one sample per thread ----
-  const int m = tile.m0 + tid;
-  const bool active = tid < B && m < K && !s_bad;
+  // ---- the rollout: the thread's samples one after another ----
   const bool five = nu == 5;
   ModelRegs M;
   M.inv_mass = d.inv_mass; M.gravity = d.gravity; M.k_omega = d.k_omega;
@@ -626,243 +634,277 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   RotorRegs RR;
   RR.arm2 = d.arm2; RR.c_tau = d.c_tau; RR.tmin = d.thrust_min; RR.tmax = d.thrust_max;
   RR.iJx = d.inv_J[0]; RR.iJy = d.inv_J[1]; RR.iJz = d.inv_J[2];
-  float Jh = 0.f, Jc = 0.f;
-  int passed = 0, first = -1;
-  if (active) {
-    Quad s;
-    s.px = x0s[0]; s.py = x0s[1]; s.pz = x0s[2];
-    s.cpx = s.cpy = s.cpz = 0.f;
-    s.vx = x0s[3]; s.vy = x0s[4]; s.vz = x0s[5];
-    s.cvx = s.cvy = s.cvz = 0.f;
-    s.qw = x0s[6]; s.qx = x0s[7]; s.qy = x0s[8]; s.qz = x0s[9];
-    s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
-    const float h = d.dt;
-    // rotor thrusts (rotor model): the controller's integrated commands
-    float Tr[4] = {0.f, 0.f, 0.f, 0.f}, Trc[4] = {0.f, 0.f, 0.f, 0.f};
-    if (ROT) {
-      const bool hr = st->has_rotor != 0;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) Tr[r] = hr ? st->rotor[r] : 0.25f * d.hover;
-    }
-    float dT2 = 0.f;
-    // objective state
-    // gate progress state: target gate, p_k - g for it (ra), its plane distance
-    int gi = 0, gate_start = 0, slot0 = 0;
-    GateF g;
-    float sa = 0.f, rax = 0.f, ray = 0.f, raz = 0.f;
-    const float q_near = d.q_near, r_near2 = d.r_near2;
-    if (OBJ == MPPI_OBJ_GATE) {
-      gi = gate_start = st->gate + s_adv;
-      slot0 = gate_slot(gi, d.n_gates, d.closed);
-      g = sG[slot0];
-      rax = s.px - g.cx;
-      ray = s.py - g.cy;
-      raz = s.pz - g.cz;
-      sa = g.nx * rax + g.ny * ray;
-    }
-    int node = 0;
-    float frac_m = 0.f, frac_c = 0.f, vth = 0.f, c_prev = 0.f;
-    if (OBJ == MPPI_OBJ_CONTOUR) {
-      node = s_j0;
-      frac_m = s_f0;
-      vth = s_vth0;
-      c_prev = st->has_prev ? st->c_last : d.hover;
-    }
-    // loop invariants in registers (the descriptor lives in shared memory)
-    const float sg0 = d.sigma[0], sg1 = d.sigma[1], sg2 = d.sigma[2], sg3 = d.sigma[3];
-    const float lo0 = d.u_min[0], lo1 = d.u_min[1], lo2 = d.u_min[2], lo3 = d.u_min[3];
-    const float hi0 = d.u_max[0], hi1 = d.u_max[1], hi2 = d.u_max[2], hi3 = d.u_max[3];
-    const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
-    // software pipeline: the next step's noise is in flight during this step
-    float z[kNU], zn[kNU];
-    if (GEN)
-      gen_noise<BF16, GEN == 1>(d, iter, m, 0, zn, five);
-    else
-      load_noise<BF16>(d, (size_t)m, zn, five);
-#pragma unroll kRolloutUnroll
-    for (int k = 0; k < N; ++k) {
-#pragma unroll
-      for (int j = 0; j < kNU; ++j) z[j] = zn[j];
-      if (k + 1 < N) {
-        if (GEN)
-          gen_noise<BF16, GEN == 1>(d, iter, m, k + 1, zn, five);
-        else
-          load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
-      }
-      const float* Uk = sU + kNU * k;
-      const float u0 = clampf(Uk[0] + sg0 * z[0], lo0, hi0);
-      const float u1 = clampf(Uk[1] + sg1 * z[1], lo1, hi1);
-      const float u2 = clampf(Uk[2] + sg2 * z[2], lo2, hi2);
-      const float u3 = clampf(Uk[3] + sg3 * z[3], lo3, hi3);
-      float stage = 0.f;
-      if (OBJ == MPPI_OBJ_TRACK) {
-        // Eq. 8 stage term on x_k and u_k
-        const float* xr = sX + kNX * k;
-        const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
-        const float sg = dot < 0.f ? -1.f : 1.f;
-        float e;
-        e = (s.px - xr[0]) - s.cpx; stage += d.Q[0] * e * e;
-        e = (s.py - xr[1]) - s.cpy; stage += d.Q[1] * e * e;
-        e = (s.pz - xr[2]) - s.cpz; stage += d.Q[2] * e * e;
-        e = (s.vx - xr[3]) - s.cvx; stage += d.Q[3] * e * e;
-        e = (s.vy - xr[4]) - s.cvy; stage += d.Q[4] * e * e;
-        e = (s.vz - xr[5]) - s.cvz; stage += d.Q[5] * e * e;
-        e = s.qw - sg * xr[6]; stage += d.Q[6] * e * e;
-        e = s.qx - sg * xr[7]; stage += d.Q[7] * e * e;
-        e = s.qy - sg * xr[8]; stage += d.Q[8] * e * e;
-        e = s.qz - sg * xr[9]; stage += d.Q[9] * e * e;
-        e = s.wx - xr[10]; stage += d.Q[10] * e * e;
-        e = s.wy - xr[11]; stage += d.Q[11] * e * e;
-        e = s.wz - xr[12]; stage += d.Q[12] * e * e;
-        const float du = ROT ? u0 : u0 - d.hover;  // rotor model: the rates themselves
-        stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
-      }
-      float near = 0.f;
-      if (OBJ == MPPI_OBJ_GATE) {
-        // Eq. 7 near-gate term on p_k and the solve's current gate g0
-        float ex = rax, ey = ray, ez = raz;
-        if (gi != gate_start) {
-          const GateF& G0 = sG[slot0];
-          ex = (s.px - G0.cx) - s.cpx;
-          ey = (s.py - G0.cy) - s.cpy;
-          ez = (s.pz - G0.cz) - s.cpz;
-        }
-        const float d0 = ex * ex + ey * ey + ez * ez;
-        near = d0 < r_near2 ? q_near * d0 : 0.f;
-      }
-      float dpx, dpy, dpz;
+#pragma unroll 1
+  for (int rep = 0; rep < spt; ++rep) {
+    const int m = tile.m0 + tid + rep * B;
+    const bool active = tid < B && m < K && !s_bad;
+    float Jh = 0.f, Jc = 0.f;
+    int passed = 0, first = -1;
+    if (active) {
+      Quad s;
+      s.px = x0s[0]; s.py = x0s[1]; s.pz = x0s[2];
+      s.cpx = s.cpy = s.cpz = 0.f;
+      s.vx = x0s[3]; s.vy = x0s[4]; s.vz = x0s[5];
+      s.cvx = s.cvy = s.cvz = 0.f;
+      s.qw = x0s[6]; s.qx = x0s[7]; s.qy = x0s[8]; s.qz = x0s[9];
+      s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
+      const float h = d.dt;
+      // rotor thrusts (rotor model): the controller's integrated commands
+      float Tr[4] = {0.f, 0.f, 0.f, 0.f}, Trc[4] = {0.f, 0.f, 0.f, 0.f};
       if (ROT) {
-        if (M.has_drag)
-          rk4_step_rotor<true>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
-        else
-          rk4_step_rotor<false>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
-      } else {
-        if (M.has_drag)
-          rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
-        else
-          rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+        const bool hr = st->has_rotor != 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Tr[r] = hr ? st->rotor[r] : 0.25f * d.hover;
       }
+      float dT2 = 0.f;
+      // objective state
+      // gate progress state: target gate, p_k - g for it (ra), its plane distance
+      int gi = 0, gate_start = 0, slot0 = 0;
+      GateF g;
+      float sa = 0.f, rax = 0.f, ray = 0.f, raz = 0.f;
+      const float q_near = d.q_near, r_near2 = d.r_near2;
       if (OBJ == MPPI_OBJ_GATE) {
-        // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
-        // with both positions taken relative to g before rounding
-        float rbx = (s.px - g.cx) - s.cpx, rby = (s.py - g.cy) - s.cpy, rbz = (s.pz - g.cz) - s.cpz;
-        stage = dpx * (rax + rbx) + dpy * (ray + rby) + dpz * (raz + rbz) + near;
-        float sb = g.nx * rbx + g.ny * rby;
-        if (sa < 0.f && sb >= 0.f) {
-          const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
-          const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
-          // crossing point on the segment, relative to the gate centre
-          const float a = sa / (sa - sb);
-          const float ex = rax + a * (rbx - rax), ey = ray + a * (rby - ray), ez = raz + a * (rbz - raz);
-          const bool open = fabsf(-g.ny * ex + g.nx * ey) <= g.hw && fabsf(ez) <= g.hh;
-          if (!open_track_done && ok_time && open) {
-            ++passed;
-            ++gi;
-            if (first < 0) first = k;
-            g = sG[gate_slot(gi, d.n_gates, d.closed)];
-            rbx = (s.px - g.cx) - s.cpx;
-            rby = (s.py - g.cy) - s.cpy;
-            rbz = (s.pz - g.cz) - s.cpz;
-            sb = g.nx * rbx + g.ny * rby;
-          }
+        gi = gate_start = st->gate + s_adv;
+        slot0 = gate_slot(gi, d.n_gates, d.closed);
+        g = sG[slot0];
+        rax = s.px - g.cx;
+        ray = s.py - g.cy;
+        raz = s.pz - g.cz;
+        sa = g.nx * rax + g.ny * ray;
+      }
+      int node = 0;
+      float frac_m = 0.f, frac_c = 0.f, vth = 0.f, c_prev = 0.f;
+      if (OBJ == MPPI_OBJ_CONTOUR) {
+        node = s_j0;
+        frac_m = s_f0;
+        vth = s_vth0;
+        c_prev = st->has_prev ? st->c_last : d.hover;
+      }
+      // loop invariants in registers (the descriptor lives in shared memory)
+      const float sg0 = d.sigma[0], sg1 = d.sigma[1], sg2 = d.sigma[2], sg3 = d.sigma[3];
+      const float lo0 = d.u_min[0], lo1 = d.u_min[1], lo2 = d.u_min[2], lo3 = d.u_min[3];
+      const float hi0 = d.u_max[0], hi1 = d.u_max[1], hi2 = d.u_max[2], hi3 = d.u_max[3];
+      const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
+      // software pipeline: the next step's noise is in flight during this step
+      float z[kNU], zn[kNU];
+      if (GEN)
+        gen_noise<BF16, GEN == 1>(d, iter, m, 0, zn, five);
+      else
+        load_noise<BF16>(d, (size_t)m, zn, five);
+#pragma unroll kRolloutUnroll
+      for (int k = 0; k < N; ++k) {
+#pragma unroll
+        for (int j = 0; j < kNU; ++j) z[j] = zn[j];
+        if (k + 1 < N) {
+          if (GEN)
+            gen_noise<BF16, GEN == 1>(d, iter, m, k + 1, zn, five);
+          else
+            load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
         }
-        rax = rbx;
-        ray = rby;
-        raz = rbz;
-        sa = sb;
-      } else if (OBJ == MPPI_OBJ_CONTOUR) {
-        // Eq. 9 with the progress state (theta, v_theta), terms on x_{k+1}
-        const float a = clampf(Uk[4] + d.sigma[4] * z[4], d.u_min[4], d.u_max[4]);
-        const float v1 = clampf(vth + a * h, 0.f, d.v_theta_max);
-        kahan_add(frac_m, frac_c, 0.5f * (vth + v1) * h);
-        float fm = frac_m - frac_c;
-        while (fm >= d.ds) {
-          frac_m -= d.ds;
-          fm = frac_m - frac_c;
-          if (++node >= d.S) node -= d.S;
-        }
-        const float fr = fm * d.inv_ds;
-        const int n1 = node + 1 >= d.S ? 0 : node + 1;
-        const float* A = path + 6 * node;
-        const float* Bn = path + 6 * n1;
-        // e = p - P(theta) with P = A + fr (B - A), formed as (p - A) - fr (B - A)
-        float Tx = A[3] + fr * (Bn[3] - A[3]), Ty = A[4] + fr * (Bn[4] - A[4]), Tz = A[5] + fr * (Bn[5] - A[5]);
-        const float rn = rsqrtf(Tx * Tx + Ty * Ty + Tz * Tz);
-        Tx *= rn; Ty *= rn; Tz *= rn;
-        const float ex = ((s.px - A[0]) - fr * (Bn[0] - A[0])) - s.cpx;
-        const float ey = ((s.py - A[1]) - fr * (Bn[1] - A[1])) - s.cpy;
-        const float ez = ((s.pz - A[2]) - fr * (Bn[2] - A[2])) - s.cpz;
-        const float et = ex * Tx + ey * Ty + ez * Tz;
-        const float cx = ex - et * Tx, cy = ey - et * Ty, cz = ez - et * Tz;
-        // thrust change: the collective command, or the rotor thrusts (rotor model)
-        const float dT = u0 - c_prev;
-        const float dTT = ROT ? dT2 : dT * dT;
-        stage = d.q_lag * et * et + d.q_cont * (cx * cx + cy * cy + cz * cz) +
-                d.q_omega[0] * s.wx * s.wx + d.q_omega[1] * s.wy * s.wy + d.q_omega[2] * s.wz * s.wz +
-                d.r_dv * a * a + d.r_dthrust * dTT - d.mu * v1;
-        c_prev = u0;
-        vth = v1;
-      } else {
-        if (k == N - 1) {
-          const float* xr = sX + kNX * N;
+        const float* Uk = sU + kNU * k;
+        const float u0 = clampf(Uk[0] + sg0 * z[0], lo0, hi0);
+        const float u1 = clampf(Uk[1] + sg1 * z[1], lo1, hi1);
+        const float u2 = clampf(Uk[2] + sg2 * z[2], lo2, hi2);
+        const float u3 = clampf(Uk[3] + sg3 * z[3], lo3, hi3);
+        float stage = 0.f;
+        if (OBJ == MPPI_OBJ_TRACK) {
+          // Eq. 8 stage term on x_k and u_k
+          const float* xr = sX + kNX * k;
           const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
           const float sg = dot < 0.f ? -1.f : 1.f;
           float e;
-          e = (s.px - xr[0]) - s.cpx; stage += d.QN[0] * e * e;
-          e = (s.py - xr[1]) - s.cpy; stage += d.QN[1] * e * e;
-          e = (s.pz - xr[2]) - s.cpz; stage += d.QN[2] * e * e;
-          e = (s.vx - xr[3]) - s.cvx; stage += d.QN[3] * e * e;
-          e = (s.vy - xr[4]) - s.cvy; stage += d.QN[4] * e * e;
-          e = (s.vz - xr[5]) - s.cvz; stage += d.QN[5] * e * e;
-          e = s.qw - sg * xr[6]; stage += d.QN[6] * e * e;
-          e = s.qx - sg * xr[7]; stage += d.QN[7] * e * e;
-          e = s.qy - sg * xr[8]; stage += d.QN[8] * e * e;
-          e = s.qz - sg * xr[9]; stage += d.QN[9] * e * e;
-          e = s.wx - xr[10]; stage += d.QN[10] * e * e;
-          e = s.wy - xr[11]; stage += d.QN[11] * e * e;
-          e = s.wz - xr[12]; stage += d.QN[12] * e * e;
+          e = (s.px - xr[0]) - s.cpx; stage += d.Q[0] * e * e;
+          e = (s.py - xr[1]) - s.cpy; stage += d.Q[1] * e * e;
+          e = (s.pz - xr[2]) - s.cpz; stage += d.Q[2] * e * e;
+          e = (s.vx - xr[3]) - s.cvx; stage += d.Q[3] * e * e;
+          e = (s.vy - xr[4]) - s.cvy; stage += d.Q[4] * e * e;
+          e = (s.vz - xr[5]) - s.cvz; stage += d.Q[5] * e * e;
+          e = s.qw - sg * xr[6]; stage += d.Q[6] * e * e;
+          e = s.qx - sg * xr[7]; stage += d.Q[7] * e * e;
+          e = s.qy - sg * xr[8]; stage += d.Q[8] * e * e;
+          e = s.qz - sg * xr[9]; stage += d.Q[9] * e * e;
+          e = s.wx - xr[10]; stage += d.Q[10] * e * e;
+          e = s.wy - xr[11]; stage += d.Q[11] * e * e;
+          e = s.wz - xr[12]; stage += d.Q[12] * e * e;
+          const float du = ROT ? u0 : u0 - d.hover;  // rotor model: the rates themselves
+          stage += d.R[0] * du * du + d.R[1] * u1 * u1 + d.R[2] * u2 * u2 + d.R[3] * u3 * u3;
         }
+        float near = 0.f;
+        if (OBJ == MPPI_OBJ_GATE) {
+          // Eq. 7 near-gate term on p_k and the solve's current gate g0
+          float ex = rax, ey = ray, ez = raz;
+          if (gi != gate_start) {
+            const GateF& G0 = sG[slot0];
+            ex = (s.px - G0.cx) - s.cpx;
+            ey = (s.py - G0.cy) - s.cpy;
+            ez = (s.pz - G0.cz) - s.cpz;
+          }
+          const float d0 = ex * ex + ey * ey + ez * ez;
+          near = d0 < r_near2 ? q_near * d0 : 0.f;
+        }
+        float dpx, dpy, dpz;
+        if (ROT) {
+          if (M.has_drag)
+            rk4_step_rotor<true>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+          else
+            rk4_step_rotor<false>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+        } else {
+          if (M.has_drag)
+            rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+          else
+            rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+        }
+        if (OBJ == MPPI_OBJ_GATE) {
+          // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
+          // with both positions taken relative to g before rounding
+          float rbx = (s.px - g.cx) - s.cpx, rby = (s.py - g.cy) - s.cpy, rbz = (s.pz - g.cz) - s.cpz;
+          stage = dpx * (rax + rbx) + dpy * (ray + rby) + dpz * (raz + rbz) + near;
+          float sb = g.nx * rbx + g.ny * rby;
+          if (sa < 0.f && sb >= 0.f) {
+            const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
+            const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
+            // crossing point on the segment, relative to the gate centre
+            const float a = sa / (sa - sb);
+            const float ex = rax + a * (rbx - rax), ey = ray + a * (rby - ray), ez = raz + a * (rbz - raz);
+            const bool open = fabsf(-g.ny * ex + g.nx * ey) <= g.hw && fabsf(ez) <= g.hh;
+            if (!open_track_done && ok_time && open) {
+              ++passed;
+              ++gi;
+              if (first < 0) first = k;
+              g = sG[gate_slot(gi, d.n_gates, d.closed)];
+              rbx = (s.px - g.cx) - s.cpx;
+              rby = (s.py - g.cy) - s.cpy;
+              rbz = (s.pz - g.cz) - s.cpz;
+              sb = g.nx * rbx + g.ny * rby;
+            }
+          }
+          rax = rbx;
+          ray = rby;
+          raz = rbz;
+          sa = sb;
+        } else if (OBJ == MPPI_OBJ_CONTOUR) {
+          // Eq. 9 with the progress state (theta, v_theta), terms on x_{k+1}
+          const float a = clampf(Uk[4] + d.sigma[4] * z[4], d.u_min[4], d.u_max[4]);
+          const float v1 = clampf(vth + a * h, 0.f, d.v_theta_max);
+          kahan_add(frac_m, frac_c, 0.5f * (vth + v1) * h);
+          float fm = frac_m - frac_c;
+          while (fm >= d.ds) {
+            frac_m -= d.ds;
+            fm = frac_m - frac_c;
+            if (++node >= d.S) node -= d.S;
+          }
+          const float fr = fm * d.inv_ds;
+          const int n1 = node + 1 >= d.S ? 0 : node + 1;
+          const float* A = path + 6 * node;
+          const float* Bn = path + 6 * n1;
+          // e = p - P(theta) with P = A + fr (B - A), formed as (p - A) - fr (B - A)
+          float Tx = A[3] + fr * (Bn[3] - A[3]), Ty = A[4] + fr * (Bn[4] - A[4]), Tz = A[5] + fr * (Bn[5] - A[5]);
+          const float rn = rsqrtf(Tx * Tx + Ty * Ty + Tz * Tz);
+          Tx *= rn; Ty *= rn; Tz *= rn;
+          const float ex = ((s.px - A[0]) - fr * (Bn[0] - A[0])) - s.cpx;
+          const float ey = ((s.py - A[1]) - fr * (Bn[1] - A[1])) - s.cpy;
+          const float ez = ((s.pz - A[2]) - fr * (Bn[2] - A[2])) - s.cpz;
+          const float et = ex * Tx + ey * Ty + ez * Tz;
+          const float cx = ex - et * Tx, cy = ey - et * Ty, cz = ez - et * Tz;
+          // thrust change: the collective command, or the rotor thrusts (rotor model)
+          const float dT = u0 - c_prev;
+          const float dTT = ROT ? dT2 : dT * dT;
+          stage = d.q_lag * et * et + d.q_cont * (cx * cx + cy * cy + cz * cz) +
+                  d.q_omega[0] * s.wx * s.wx + d.q_omega[1] * s.wy * s.wy + d.q_omega[2] * s.wz * s.wz +
+                  d.r_dv * a * a + d.r_dthrust * dTT - d.mu * v1;
+          c_prev = u0;
+          vth = v1;
+        } else {
+          if (k == N - 1) {
+            const float* xr = sX + kNX * N;
+            const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
+            const float sg = dot < 0.f ? -1.f : 1.f;
+            float e;
+            e = (s.px - xr[0]) - s.cpx; stage += d.QN[0] * e * e;
+            e = (s.py - xr[1]) - s.cpy; stage += d.QN[1] * e * e;
+            e = (s.pz - xr[2]) - s.cpz; stage += d.QN[2] * e * e;
+            e = (s.vx - xr[3]) - s.cvx; stage += d.QN[3] * e * e;
+            e = (s.vy - xr[4]) - s.cvy; stage += d.QN[4] * e * e;
+            e = (s.vz - xr[5]) - s.cvz; stage += d.QN[5] * e * e;
+            e = s.qw - sg * xr[6]; stage += d.QN[6] * e * e;
+            e = s.qx - sg * xr[7]; stage += d.QN[7] * e * e;
+            e = s.qy - sg * xr[8]; stage += d.QN[8] * e * e;
+            e = s.qz - sg * xr[9]; stage += d.QN[9] * e * e;
+            e = s.wx - xr[10]; stage += d.QN[10] * e * e;
+            e = s.wy - xr[11]; stage += d.QN[11] * e * e;
+            e = s.wz - xr[12]; stage += d.QN[12] * e * e;
+          }
+        }
+        stage += limit_penalty(w_limit, omega_max, z_floor, s);
+        kahan_add(Jh, Jc, stage);
       }
-      stage += limit_penalty(w_limit, omega_max, z_floor, s);
-      kahan_add(Jh, Jc, stage);
     }
-  }
 
-  // ---- per-sample outputs and the block's share of Eq. 4 ----
-  const double Jd = (double)Jh - (double)Jc;
-  const float Jf = Jh - Jc;
-  const bool valid = active && isfinite(Jh) && isfinite(Jc) && isfinite(Jf);
-  if (active) {
-    d.J[m] = Jd;
-    d.info[m] = passed | ((first + 1) << 16);
-  }
+    // per-sample outputs; the cost pair stays in shared memory for Eq. 4
+    const bool valid = active && isfinite(Jh) && isfinite(Jc) && isfinite(Jh - Jc);
+    if (active) {
+      d.J[m] = (double)Jh - (double)Jc;
+      d.info[m] = passed | ((first + 1) << 16);
+    }
+    if (tid < B) {
+      sJ[tid + rep * B] = valid ? Jh : NAN;
+      sJ[TS + tid + rep * B] = Jc;
+    }
+  }  // samples of this thread
+
+  // ---- the block's share of Eq. 4 ----
   const int acc = d.accum;
   // (with GEN 1 the epilogue reads noise other threads of this block stored;
   // the barriers inside the block reductions make those stores visible)
   double m_t, S_t;  // tile minimum and sum of exp weights (packed (hi, lo) unless FP64)
-  float e = 0.f;
+  const int own = tid < B ? spt : 0;  // this thread's entries of sJ / sE
   if (acc == MPPI_ACC_F64) {
-    m_t = block_min_d(valid ? Jd : INFINITY, red);
-    if (valid && !isinf(m_t)) e = expf(-(float)(Jd - m_t) * d.inv_lambda);
-    if (tid < B) sE[tid] = e;
-    S_t = block_sum_d((double)e, red);  // also publishes sE
+    double mloc = INFINITY;
+    for (int r = 0; r < own; ++r) {
+      const int i = tid + r * B;
+      if (isfinite(sJ[i])) mloc = fmin(mloc, (double)sJ[i] - (double)sJ[TS + i]);
+    }
+    m_t = block_min_d(mloc, red);
+    double se = 0.0;
+    for (int r = 0; r < own; ++r) {
+      const int i = tid + r * B;
+      float e = 0.f;
+      if (isfinite(sJ[i]) && !isinf(m_t))
+        e = expf(-(float)(((double)sJ[i] - (double)sJ[TS + i]) - m_t) * d.inv_lambda);
+      sE[i] = e;
+      se += (double)e;
+    }
+    S_t = block_sum_d(se, red);  // also publishes sE
   } else {
     // any common shift leaves Eq. 4 unchanged: the binary32 minimum of the
     // rounded costs serves; J - m_t is formed from the compensated pair
     float* redf = reinterpret_cast<float*>(red);
-    const float mf = block_min_f(valid ? Jf : INFINITY, redf);
-    if (valid && !isinf(mf)) e = expf(-(((Jh - mf) - Jc) * d.inv_lambda));
-    if (tid < B) sE[tid] = e;
-    float sh = e, sl = 0.f;
+    float mloc = INFINITY;
+    for (int r = 0; r < own; ++r) {
+      const int i = tid + r * B;
+      if (isfinite(sJ[i])) mloc = fminf(mloc, sJ[i] - sJ[TS + i]);
+    }
+    const float mf = block_min_f(mloc, redf);
+    float sh = 0.f, sl = 0.f;
+    for (int r = 0; r < own; ++r) {
+      const int i = tid + r * B;
+      float e = 0.f;
+      if (isfinite(sJ[i]) && !isinf(mf)) e = expf(-(((sJ[i] - mf) - sJ[TS + i]) * d.inv_lambda));
+      sE[i] = e;
+      if (r == 0)
+        sh = e;
+      else
+        add2(sh, sl, e, 0.f);
+    }
     block_sum2_f(sh, sl, redf);  // also publishes sE
     m_t = (double)mf;
     S_t = pack2(sh, sl);
   }
 
   // ---- weighted deviation sums per (step, input) of this tile (Eq. 5) ----
-  const int nvalid = min(B, K - tile.m0);
+  const int nvalid = min(TS, K - tile.m0);
   const int NNU = N * kNU;
-  const int tile_in_solve = tile.m0 / B;
+  const int tile_in_solve = tile.m0 / TS;
   double* myP = d.part_P + (size_t)tile_in_solve * NNU;
   // each warp takes kEpiRows steps at a time, kEpiLanes lanes per step: a lane
   // sums every kEpiLanes-th sample of the tile, then the lanes of a step

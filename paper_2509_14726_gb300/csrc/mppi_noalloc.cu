@@ -114,9 +114,9 @@ __global__ void noalloc_setup_kernel(SolveDesc d, SolveDesc* d_desc, const float
   for (int i = tid; i < n_tickets; i += nth) d.ticket[i] = 0u;
 }
 
-__global__ void noalloc_tiles_kernel(Tile* tiles, int T, int block) {
+__global__ void noalloc_tiles_kernel(Tile* tiles, int T, int tile) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < T) tiles[i] = Tile{0, i * block};
+  if (i < T) tiles[i] = Tile{0, i * tile};
 }
 
 }  // namespace
@@ -138,6 +138,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32)
     return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
   if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return fail(MPPI_ERR_ARG, "noise dtype");
+  if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
+    return fail(MPPI_ERR_ARG, "samples_per_thread out of range");
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.objective == MPPI_OBJ_GATE && (d_track->n_gates < 1 || !d_track->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs gates");
@@ -197,7 +199,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.passcnt = reinterpret_cast<int32_t*>(b + L.passcnt);
   d.xref = reinterpret_cast<float*>(b + L.xref);
   d.block = block;
-  d.n_tiles = (p.K + block - 1) / block;
+  d.n_tiles = (p.K + tile_samples(d) - 1) / tile_samples(d);  // at most the layout's tiles
   d.ext_noise = 0;
   int sq = 1;
   while (sq * sq < d.n_tiles) ++sq;
@@ -207,7 +209,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   Tile* d_tiles = reinterpret_cast<Tile*>(b + L.tiles);
   (void)cudaGetLastError();
   noalloc_setup_kernel<<<4, 256, 0, s>>>(d, d_desc, d_U, iter, gate, n_tickets);
-  noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, block);
+  noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, tile_samples(d));
   add_launches(2);
   if (cudaGetLastError() != cudaSuccess) return fail(MPPI_ERR_CUDA, "set-up kernel launch failed");
   if (d.noise_gen == MPPI_NOISEGEN_KERNEL &&
@@ -220,7 +222,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.t0v = t0;
   io.u0 = d_u0;
   io.status = nullptr;
-  const uint32_t smem = rollout_smem_bytes(p.N, p.objective, d.S, block, d.n_tiles > 32 ? d.n_tiles : 32);
+  const uint32_t smem =
+      rollout_smem_bytes(p.N, p.objective, d.S, tile_samples(d), d.n_tiles > 32 ? d.n_tiles : 32);
   if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen, d.rotor) !=
       cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");

@@ -310,6 +310,8 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_REGEN ||
       (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32))
     return sfail(MPPI_ERR_ARG, "bad noise generation mode");
+  if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
+    return sfail(MPPI_ERR_ARG, "samples_per_thread outside [0, %d]", MPPI_MAX_SPT);
   if (track->n_gates < 0 || track->n_gates > MPPI_MAX_GATES) return sfail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.objective == MPPI_OBJ_GATE && (track->n_gates < 1 || !track->gates)) return sfail(MPPI_ERR_ARG, "no gates");
   if (p.objective == MPPI_OBJ_CONTOUR && (track->S < 2 || !track->path || !(track->L > 0)))
@@ -447,7 +449,8 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     Request r = s->queue.front();
     s->queue.pop_front();
     Drone& d = s->drones[r.drone];
-    const int T = (r.K + d.block - 1) / d.block;
+    const int TS = d.block * d.hd.spt;
+    const int T = (r.K + TS - 1) / TS;
     if (blocked || d.busy || (int)batch.size() >= s->max_batch || tiles + T > s->max_tiles) {
       keep.push_back(r);
       continue;
@@ -499,7 +502,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     const Scratch sc = scratch_for(r.K, r.N, d.block, d.nu == 5, dd.noise_bf16, dd.noise_gen);
     dd.K = r.K;
     dd.N = r.N;
-    dd.n_tiles = (r.K + d.block - 1) / d.block;
+    dd.n_tiles = (r.K + tile_samples(dd) - 1) / tile_samples(dd);
     const bool stored = dd.noise_gen != MPPI_NOISEGEN_REGEN;
     dd.Z4 = (stored && !dd.noise_bf16) ? reinterpret_cast<float4*>(b + sc.Z) : nullptr;
     dd.Zb = (stored && dd.noise_bf16) ? reinterpret_cast<uint2*>(b + sc.Z) : nullptr;
@@ -539,8 +542,8 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
       groups.push_back(Group{dd.objective, dd.noise_bf16, dd.block, dd.noise_gen, dd.nominal_sample, dd.rotor, {}, 0});
       g = (int)groups.size() - 1;
     }
-    for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * dd.block});
-    groups[g].smem = std::max(groups[g].smem, rollout_smem_bytes(dd.N, dd.objective, dd.S, dd.block,
+    for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * tile_samples(dd)});
+    groups[g].smem = std::max(groups[g].smem, rollout_smem_bytes(dd.N, dd.objective, dd.S, tile_samples(dd),
                                                                  dd.n_tiles > 32 ? dd.n_tiles : 32));
     if (dd.objective == MPPI_OBJ_GATE) which.push_back(i);
   }

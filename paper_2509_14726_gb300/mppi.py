@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("temporal_rule", I32), ("q_lag", F), ("q_cont", F), ("q_omega", F * 3), ("r_dv", F),
                 ("r_dthrust", F), ("mu", F), ("v_theta_max", F), ("theta_back", F), ("theta_ahead", F),
                 ("Q", F * 13), ("QN", F * 13), ("R", F * 4), ("noise_dtype", I32), ("accum", I32), ("block", I32),
-                ("N_cap", I32), ("K_cap", I32), ("noise_gen", I32), ("nominal_sample", I32), ("warm_start", I32)]
+                ("N_cap", I32), ("K_cap", I32), ("noise_gen", I32), ("nominal_sample", I32), ("warm_start", I32),
+                ("samples_per_thread", I32)]
 
 
 class TrackC(C.Structure):
@@ -166,7 +167,7 @@ def make_model(mc: W.ModelConfig) -> Model:
 
 
 def make_params(sc: W.SolveConfig, noise_dtype: int = NOISE_F32, accum: int = ACC_KAHAN32, block: int = 128,
-                N_cap: int = 0, K_cap: int = 0, noise_gen: Optional[int] = None) -> Params:
+                N_cap: int = 0, K_cap: int = 0, noise_gen: Optional[int] = None, spt: int = 1) -> Params:
     p = Params()
     p.objective, p.K, p.N = sc.objective, sc.K, sc.N
     p.dt, p.lam = sc.dt, sc.lam
@@ -183,6 +184,7 @@ def make_params(sc: W.SolveConfig, noise_dtype: int = NOISE_F32, accum: int = AC
     p.noise_dtype, p.accum, p.block, p.N_cap, p.K_cap = noise_dtype, accum, block, N_cap, K_cap
     p.noise_gen = NOISEGEN_DEFAULT if noise_gen is None else noise_gen
     p.nominal_sample, p.warm_start = int(sc.nominal_sample), int(sc.warm_start)
+    p.samples_per_thread = int(spt)
     return p
 
 
@@ -424,10 +426,10 @@ class Controller:
 
     def __init__(self, mc: W.ModelConfig, sc: W.SolveConfig, track: W.Track, noise_dtype: int = NOISE_F32,
                  accum: int = ACC_KAHAN32, block: int = 128, N_cap: int = 0, K_cap: int = 0,
-                 noise_gen: Optional[int] = None):
+                 noise_gen: Optional[int] = None, spt: int = 1):
         self.mc, self.sc, self.track = mc, sc, track
         self.model = make_model(mc)
-        self.params = make_params(sc, noise_dtype, accum, block, N_cap, K_cap, noise_gen)
+        self.params = make_params(sc, noise_dtype, accum, block, N_cap, K_cap, noise_gen, spt)
         self.tables = TrackArrays(track)
         self.h = mppi_create(self.model, self.params, self.tables)
         self.K, self.N = sc.K, sc.N
@@ -565,13 +567,14 @@ class Server:
         self.h = h.value
         self._keep = []
 
-    def add_drone(self, mc, sc, track, K_cap: int, N_cap: int, block: int = 128, noise_gen: Optional[int] = None) -> int:
+    def add_drone(self, mc, sc, track, K_cap: int, N_cap: int, block: int = 128, noise_gen: Optional[int] = None,
+                  spt: int = 1) -> int:
         tables = TrackArrays(track)
         self._keep.append(tables)
         d = I32()
         _check(load().mppi_server_add_drone(C.c_void_p(self.h), C.byref(make_model(mc)),
                                             C.byref(make_params(sc, block=block, N_cap=N_cap, K_cap=K_cap,
-                                                                noise_gen=noise_gen)),
+                                                                noise_gen=noise_gen, spt=spt)),
                                             C.byref(tables.c), C.byref(d)))
         return int(d.value)
 

@@ -81,6 +81,10 @@ def test_error_paths_need_no_device(lib_path):
     m.kind = 1
     L.mppi_default_params(ctypes.byref(p), 0, 16, 20, 0.05)
     assert L.mppi_create(ctypes.byref(m), ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == mppi.MPPI_ERR_ARG
+    m.kind = 0
+    p.samples_per_thread = 9
+    assert L.mppi_create(ctypes.byref(m), ctypes.byref(p), ctypes.byref(t), ctypes.byref(h)) == mppi.MPPI_ERR_ARG
+    assert b"samples_per_thread" in L.mppi_last_error()
     assert L.mppi_solve(None, None, 0.0, None, None) == mppi.MPPI_ERR_ARG
     assert L.mppi_destroy(None) == 0
 
