@@ -47,11 +47,11 @@ FLOPS_PER_STEP = {0: 423.0, 1: 491.0, 2: 478.0}
 FLOPS_PER_STEP_ROTOR = {0: 531.0, 1: 599.0, 2: 586.0}
 
 
-def measured_traffic(steps_by_objective):
-    """DRAM bytes of the three rollout launches of one step, from the ncu
-    capture recorded under profiles/ (bytes per rollout step per objective,
-    scaled by this workload's K x N), or None when the kernel source is not
-    the one that was captured."""
+def _captured_per_step(kind: str):
+    """Per-rollout-step figures of one kind ("bytes_per_step" or
+    "fp32_ops_per_step") by objective, from the ncu capture recorded under
+    profiles/, or None when the kernel source is not the one that was
+    captured."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.txt")
     src = os.path.join(ROOT, "paper_2509_14726_gb300", "csrc")
@@ -67,11 +67,30 @@ def measured_traffic(steps_by_objective):
     rec = {ln[0]: ln[1:] for ln in lines if ln[0] == "source_sha256"}
     if rec.get("source_sha256", [None])[0] != h.hexdigest():
         return None
-    per = {ln[1]: float(ln[2]) for ln in lines if ln[0] == "bytes_per_step"}
+    per = {ln[1]: float(ln[2]) for ln in lines if ln[0] == kind}
     names = {0: "gate", 1: "contour", 2: "track"}
     if any(names[o] not in per for o in (0, 1, 2)):
         return None
-    return sum(per[names[o]] * steps_by_objective[o] for o in (0, 1, 2))
+    return {o: per[names[o]] for o in (0, 1, 2)}
+
+
+def measured_traffic(steps_by_objective):
+    """DRAM bytes of the three rollout launches of one step: the captured
+    bytes per rollout step per objective scaled by this workload's K x N."""
+    per = _captured_per_step("bytes_per_step")
+    if per is None:
+        return None
+    return sum(per[o] * steps_by_objective[o] for o in (0, 1, 2))
+
+
+def measured_fp32_ops(steps_by_objective):
+    """FP32 operations (FFMA = 2, FADD, FMUL) the three rollout launches of
+    one step execute, by ncu's SASS counters per rollout step scaled by this
+    workload's K x N; with the per-step figures."""
+    per = _captured_per_step("fp32_ops_per_step")
+    if per is None:
+        return None, None
+    return sum(per[o] * steps_by_objective[o] for o in (0, 1, 2)), per
 
 
 def paper_table1_latency(M, W, reps: int = 300) -> dict:
@@ -454,6 +473,13 @@ def main():
         roofline["frac_at_sampled_clock"] = achieved / (n_sm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     noise_bytes = sum(it.K * it.N * (16 + (4 if it.objective == 1 else 0)) for it in items)
     roofline["noise_kernel_gbs"] = noise_bytes / (float(prof[0]) / 1e3) / 1e9 if prof[0] > 0 else None
+    # the same fraction on the FP32 operations the hardware counted (ncu SASS
+    # counters of the captured kernel: FFMA = 2, FADD, FMUL; min/max, compares
+    # and MUFU not counted), beside the algorithmic count above
+    ops, per = measured_fp32_ops(steps_by_obj)
+    if ops is not None:
+        roofline["ncu_fp32_ops_per_step"] = {n: per[o] for o, n in ((0, "gate"), (1, "contour"), (2, "track"))}
+        roofline["frac_ncu_fp32_ops"] = ops / (roll_ms / 1e3) / 1e12 / peak
 
     # ---- the same batch with the rotor-thrust-rate model (Eq. 2 as printed) ----
     rotor_out = None
