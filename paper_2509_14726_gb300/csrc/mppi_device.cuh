@@ -495,7 +495,8 @@ __device__ __forceinline__ float limit_penalty(float wlim, float wmax, float zf,
 }
 
 // gate frame in shared memory: centre, plane normal (horizontal), half sizes
-struct GateF {
+// (16-byte aligned: read as two float4)
+struct __align__(16) GateF {
   float cx, cy, cz, nx, ny, hw, hh, pad;
 };
 

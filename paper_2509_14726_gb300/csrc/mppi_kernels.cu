@@ -33,6 +33,16 @@ namespace mppi {
 constexpr int kNoiseUnroll = MPPI_NOISE_UNROLL;
 constexpr int kRolloutUnroll = MPPI_ROLLOUT_UNROLL;
 
+// A shared-memory vector load the compiler keeps where it is written (not
+// hoisted out of a loop into registers).
+__device__ __forceinline__ float4 lds4_volatile(const float4* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return v;
+}
+
 // bounded wait on an mbarrier phase; returns false after ~timeout_ns
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
@@ -171,6 +181,18 @@ __device__ __forceinline__ bool through_opening(const GateF& g, float sa, float 
   const float ex = ax + a * dx - g.cx, ey = ay + a * dy - g.cy, ez = az + a * dz - g.cz;
   const float lat = -g.ny * ex + g.nx * ey;
   return fabsf(lat) <= g.hw && fabsf(ez) <= g.hh;
+}
+
+// A gate frame read from shared memory as two 16-byte vectors into scalar
+// fields.  (A whole-struct copy from a dynamically indexed element was kept
+// as a stack object and read back from local memory at every use.)
+__device__ __forceinline__ GateF load_gate(const GateF* table, int i) {
+  const float4* p = reinterpret_cast<const float4*>(table + i);
+  const float4 a = p[0], b = p[1];
+  GateF g;
+  g.cx = a.x; g.cy = a.y; g.cz = a.z; g.nx = a.w;
+  g.ny = b.x; g.hw = b.y; g.hh = b.z; g.pad = b.w;
+  return g;
 }
 
 __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
@@ -463,6 +485,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   __shared__ __align__(8) uint64_t mbar;
   __shared__ double red[32];
   __shared__ float x0s[kNX];
+  __shared__ float4 sBnd[5];  // (sigma, u_min, u_max, 0) per input; (w_limit, omega_max, z_floor, 0)
   __shared__ int s_adv, s_last, s_group_last, s_bad;
   __shared__ double s_theta0, s_m, s_S;
   __shared__ float s_vth0, s_f0;
@@ -481,6 +504,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   if (tid < kNX) x0s[tid] = io.x0 ? io.x0[(size_t)tile.solve * kNX + tid] : io.x0v[tid];
   __syncthreads();
   const SolveDesc& d = sd;
+  if (tid < 4) sBnd[tid] = make_float4(d.sigma[tid], d.u_min[tid], d.u_max[tid], 0.f);
+  if (tid == 4) sBnd[4] = make_float4(d.w_limit, d.omega_max, d.z_floor, 0.f);
   const int K = d.K, N = d.N, nu = d.nu, B = d.block;
   const int path_smem = path_fits_smem(d.S);
   // the tile: TS = B spt samples; thread tid runs m0 + tid + rep B, rep < spt
@@ -526,7 +551,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       // the plant's own pass of the current gate since the last solve
       int adv = 0;
       if (st->has_prev && !(d.closed == 0 && st->gate >= d.n_gates)) {
-        const GateF g = sG[gate_slot(st->gate, d.n_gates, d.closed)];
+        const GateF g = load_gate(sG, gate_slot(st->gate, d.n_gates, d.closed));
         const float* p0 = st->prev_x0;
         const float sa = plane_dist(g, p0[0], p0[1]), sb = plane_dist(g, x0s[0], x0s[1]);
         if (sa < 0.f && sb >= 0.f &&
@@ -660,17 +685,18 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       // objective state
       // gate progress state: target gate, p_k - g for it (ra), its plane distance
       int gi = 0, gate_start = 0, slot0 = 0;
-      GateF g;
+      // the target gate's frame, read from shared memory where it is used
+      const GateF* gp = sG;
       float sa = 0.f, rax = 0.f, ray = 0.f, raz = 0.f;
       const float q_near = d.q_near, r_near2 = d.r_near2;
       if (OBJ == MPPI_OBJ_GATE) {
         gi = gate_start = st->gate + s_adv;
         slot0 = gate_slot(gi, d.n_gates, d.closed);
-        g = sG[slot0];
-        rax = s.px - g.cx;
-        ray = s.py - g.cy;
-        raz = s.pz - g.cz;
-        sa = g.nx * rax + g.ny * ray;
+        gp = sG + slot0;
+        rax = s.px - gp->cx;
+        ray = s.py - gp->cy;
+        raz = s.pz - gp->cz;
+        sa = gp->nx * rax + gp->ny * ray;
       }
       int node = 0;
       float frac_m = 0.f, frac_c = 0.f, vth = 0.f, c_prev = 0.f;
@@ -681,10 +707,6 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         c_prev = st->has_prev ? st->c_last : d.hover;
       }
       // loop invariants in registers (the descriptor lives in shared memory)
-      const float sg0 = d.sigma[0], sg1 = d.sigma[1], sg2 = d.sigma[2], sg3 = d.sigma[3];
-      const float lo0 = d.u_min[0], lo1 = d.u_min[1], lo2 = d.u_min[2], lo3 = d.u_min[3];
-      const float hi0 = d.u_max[0], hi1 = d.u_max[1], hi2 = d.u_max[2], hi3 = d.u_max[3];
-      const float w_limit = d.w_limit, omega_max = d.omega_max, z_floor = d.z_floor;
       // software pipeline: the next step's noise is in flight during this step
       float z[kNU], zn[kNU];
       if (GEN)
@@ -702,10 +724,16 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
             load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
         }
         const float* Uk = sU + kNU * k;
-        const float u0 = clampf(Uk[0] + sg0 * z[0], lo0, hi0);
-        const float u1 = clampf(Uk[1] + sg1 * z[1], lo1, hi1);
-        const float u2 = clampf(Uk[2] + sg2 * z[2], lo2, hi2);
-        const float u3 = clampf(Uk[3] + sg3 * z[3], lo3, hi3);
+        // sampling (Eq. 3 with the clamp): sigma and the input bounds are
+        // read from shared memory every step rather than held in 12
+        // registers (the rollout is built for 96 registers; held, they
+        // pushed the gate-progress rollout into spills)
+        const float4 b0 = lds4_volatile(sBnd), b1 = lds4_volatile(sBnd + 1), b2 = lds4_volatile(sBnd + 2),
+                     b3 = lds4_volatile(sBnd + 3);
+        const float u0 = clampf(Uk[0] + b0.x * z[0], b0.y, b0.z);
+        const float u1 = clampf(Uk[1] + b1.x * z[1], b1.y, b1.z);
+        const float u2 = clampf(Uk[2] + b2.x * z[2], b2.y, b2.z);
+        const float u3 = clampf(Uk[3] + b3.x * z[3], b3.y, b3.z);
         float stage = 0.f;
         if (OBJ == MPPI_OBJ_TRACK) {
           // Eq. 8 stage term on x_k and u_k
@@ -757,25 +785,25 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         if (OBJ == MPPI_OBJ_GATE) {
           // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
           // with both positions taken relative to g before rounding
-          float rbx = (s.px - g.cx) - s.cpx, rby = (s.py - g.cy) - s.cpy, rbz = (s.pz - g.cz) - s.cpz;
+          float rbx = (s.px - gp->cx) - s.cpx, rby = (s.py - gp->cy) - s.cpy, rbz = (s.pz - gp->cz) - s.cpz;
           stage = dpx * (rax + rbx) + dpy * (ray + rby) + dpz * (raz + rbz) + near;
-          float sb = g.nx * rbx + g.ny * rby;
+          float sb = gp->nx * rbx + gp->ny * rby;
           if (sa < 0.f && sb >= 0.f) {
             const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
             const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
             // crossing point on the segment, relative to the gate centre
             const float a = sa / (sa - sb);
             const float ex = rax + a * (rbx - rax), ey = ray + a * (rby - ray), ez = raz + a * (rbz - raz);
-            const bool open = fabsf(-g.ny * ex + g.nx * ey) <= g.hw && fabsf(ez) <= g.hh;
+            const bool open = fabsf(-gp->ny * ex + gp->nx * ey) <= gp->hw && fabsf(ez) <= gp->hh;
             if (!open_track_done && ok_time && open) {
               ++passed;
               ++gi;
               if (first < 0) first = k;
-              g = sG[gate_slot(gi, d.n_gates, d.closed)];
-              rbx = (s.px - g.cx) - s.cpx;
-              rby = (s.py - g.cy) - s.cpy;
-              rbz = (s.pz - g.cz) - s.cpz;
-              sb = g.nx * rbx + g.ny * rby;
+              gp = sG + gate_slot(gi, d.n_gates, d.closed);
+              rbx = (s.px - gp->cx) - s.cpx;
+              rby = (s.py - gp->cy) - s.cpy;
+              rbz = (s.pz - gp->cz) - s.cpz;
+              sb = gp->nx * rbx + gp->ny * rby;
             }
           }
           rax = rbx;
@@ -835,7 +863,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
             e = s.wz - xr[12]; stage += d.QN[12] * e * e;
           }
         }
-        stage += limit_penalty(w_limit, omega_max, z_floor, s);
+        {
+          const float4 bl = lds4_volatile(sBnd + 4);
+          stage += limit_penalty(bl.x, bl.y, bl.z, s);
+        }
         kahan_add(Jh, Jc, stage);
       }
     }
@@ -1131,7 +1162,7 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
     s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
     s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
     int gi = st->gate, passed = 0;
-    GateF g = sG[w][gate_slot(gi, d.n_gates, d.closed)];
+    GateF g = load_gate(sG[w], gate_slot(gi, d.n_gates, d.closed));
     float sa = plane_dist(g, s.px, s.py);
     d.passcnt[0] = 0;
     RotorRegs RR;
@@ -1161,7 +1192,7 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
         if (!open_track_done && ok_time && through_opening(g, sa, sb, ax, ay, az, bx - ax, by - ay, bz - az)) {
           ++passed;
           ++gi;
-          g = sG[w][gate_slot(gi, d.n_gates, d.closed)];
+          g = load_gate(sG[w], gate_slot(gi, d.n_gates, d.closed));
           sa = plane_dist(g, bx, by);
         } else {
           sa = sb;
