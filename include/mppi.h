@@ -206,7 +206,11 @@ int mppi_solve_batch(int32_t n, const mppi_handle* hs, const float* x0s, const d
  * captures it as one serial chain; 0 launches without a graph. */
 int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_batch* out);
 int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* stream, float* u0s_out);
-/* device-side form: d_x0s [n][13], d_t0s [n], d_u0s [n][5]; asynchronous */
+/* device-side form: d_x0s [n][13], d_t0s [n], d_u0s [n][5]; asynchronous.
+ * With a graph plan, the first call with a given (d_x0s, d_t0s, d_u0s) set
+ * captures the launch sequence on those buffers; later calls with the same
+ * set launch it with no copies.  A plan keeps graphs for 4 sets; calls with
+ * other sets copy through the plan's own buffers (two copies in, one out). */
 int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s, void* stream,
                            float* d_u0s);
 int mppi_batch_destroy(mppi_batch b);

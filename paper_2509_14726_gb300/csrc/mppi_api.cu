@@ -170,7 +170,20 @@ struct mppi_batch_s {
   float* d_x0s = nullptr;
   double* d_t0s = nullptr;
   float* d_u0s = nullptr;
+  // graphs captured on the caller's own device buffers: a call whose
+  // (x0, t0, u0) pointers match one of them launches it with no copies
+  struct DevExec {
+    const float* x0;
+    const double* t0;
+    float* u0;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  };
+  std::vector<DevExec> dev_execs;
 };
+
+// caller pointer sets a plan keeps graphs for; further sets use the copy path
+constexpr size_t kMaxDevExecs = 4;
 
 namespace {
 
@@ -904,6 +917,34 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
   return MPPI_OK;
 }
 
+// Captures the plan's launch sequence reading x0 / t0 from and writing u0 to
+// the given device buffers (no host-mapped status) and instantiates it.
+static int capture_dev_graph(mppi_batch b, const float* x0, const double* t0, float* u0, cudaGraph_t* g,
+                             cudaGraphExec_t* e) {
+  LaunchIO iod;
+  memset(&iod, 0, sizeof iod);
+  iod.x0 = x0;
+  iod.t0 = t0;
+  iod.u0 = u0;
+  iod.status = nullptr;
+  if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(MPPI_ERR_CUDA, "begin capture failed");
+  const int rc = batch_enqueue_branches(b, iod, b->cap_stream);
+  const cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
+  if (rc || e2 != cudaSuccess || e3 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(MPPI_ERR_CUDA, "graph capture failed");
+  }
+  if (cudaGraphInstantiate(e, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(MPPI_ERR_CUDA, "graph instantiation failed");
+  }
+  *g = graph;
+  return MPPI_OK;
+}
+
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom));
   for (const auto& g : b->rollout_groups)
@@ -917,6 +958,10 @@ int mppi_batch_destroy(mppi_batch b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->exec_dev) cudaGraphExecDestroy(b->exec_dev);
   if (b->graph_dev) cudaGraphDestroy(b->graph_dev);
+  for (const auto& de : b->dev_execs) {
+    cudaGraphExecDestroy(de.exec);
+    cudaGraphDestroy(de.graph);
+  }
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (cudaStream_t bs : b->branch_streams) cudaStreamDestroy(bs);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -1079,20 +1124,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
                           cudaGetErrorString(e2), cudaGetErrorString(e3)));
     if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
       return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
-    LaunchIO iod;
-    memset(&iod, 0, sizeof iod);
-    iod.x0 = b->d_x0s;
-    iod.t0 = b->d_t0s;
-    iod.u0 = b->d_u0s;
-    iod.status = nullptr;
-    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
-    int rc3 = batch_enqueue_branches(b, iod, b->cap_stream);
-    cudaError_t f2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
-    cudaError_t f3 = cudaStreamEndCapture(b->cap_stream, &b->graph_dev);
-    if (rc3 || f2 || f3) return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed"));
-    if (cudaGraphInstantiate(&b->exec_dev, b->graph_dev, 0) != cudaSuccess)
-      return cleanup(fail(MPPI_ERR_CUDA, "graph instantiation failed"));
+    int rc3 = capture_dev_graph(b, b->d_x0s, b->d_t0s, b->d_u0s, &b->graph_dev, &b->exec_dev);
+    if (rc3) return cleanup(rc3);
   }
   *out = b;
   return MPPI_OK;
@@ -1199,6 +1232,23 @@ int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s
   io.status = nullptr;
   if (!d_t0s) return fail(MPPI_ERR_ARG, "d_t0s is required");
   if (b->use_graph && b->exec_dev) {
+    // the caller's buffers directly, through a graph captured on them
+    cudaGraphExec_t ex = nullptr;
+    for (const auto& de : b->dev_execs)
+      if (de.x0 == d_x0s && de.t0 == d_t0s && de.u0 == d_u0s) ex = de.exec;
+    if (!ex && b->dev_execs.size() < kMaxDevExecs) {
+      mppi_batch_s::DevExec de{d_x0s, d_t0s, d_u0s, nullptr, nullptr};
+      rc = capture_dev_graph(b, d_x0s, d_t0s, d_u0s, &de.graph, &de.exec);
+      if (rc) return rc;
+      b->dev_execs.push_back(de);
+      ex = de.exec;
+    }
+    if (ex) {
+      CU(cudaGraphLaunch(ex, s));
+      add_launches(b->kernels_per_solve);
+      return MPPI_OK;
+    }
+    // more pointer sets than kept graphs: copy through the plan's own buffers
     CU(cudaMemcpyAsync(b->d_x0s, d_x0s, sizeof(float) * 13 * b->n, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(b->d_t0s, d_t0s, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, s));
     CU(cudaGraphLaunch(b->exec_dev, s));
