@@ -470,6 +470,10 @@ __device__ void merge_partials(const SolveDesc& d, const MergeIn in, int n, int 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
 
 // lanes that share one step in the epilogue's weighted sums (power of two <= 32)
+#ifndef MPPI_EPI_BATCH
+#define MPPI_EPI_BATCH 4
+#endif
+static_assert(MPPI_EPI_BATCH >= 1 && MPPI_EPI_BATCH <= 16, "MPPI_EPI_BATCH must be in [1, 16]");
 #ifndef MPPI_EPI_LANES
 #define MPPI_EPI_LANES 8
 #endif
@@ -940,7 +944,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   // each warp takes kEpiRows steps at a time, kEpiLanes lanes per step: a lane
   // sums every kEpiLanes-th sample of the tile, then the lanes of a step
   // reduce in a fixed order within their group (log2(kEpiLanes) levels)
-  constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes;
+  // (regenerated normals are computed, not loaded: nothing to overlap)
+  constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes, kEpiBatch = GEN == 2 ? 1 : MPPI_EPI_BATCH;
   const int sub = lane / kEpiLanes, sl = lane % kEpiLanes;
   for (int k0 = wid * kEpiRows; k0 < N; k0 += nw * kEpiRows) {
     const int k = k0 + sub;
@@ -951,24 +956,36 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
 #pragma unroll
     for (int j = 0; j < kNU; ++j) { hi[j] = 0.f; lo[j] = 0.f; dacc[j] = 0.0; }
     if (row_ok) {
-      for (int i = sl; i < nvalid; i += kEpiLanes) {
-        const float w = sE[i];
-        float zz[kNU];
-        if (GEN == 2)
-          gen_noise<BF16, false>(d, iter, tile.m0 + i, k, zz, five);
-        else
-          load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + i, zz, five);
+      // kEpiBatch samples per round trip: their weights and normals are all
+      // requested before the first is used (a lone block otherwise waits one
+      // L2 latency per sample), then summed in sample order
+      for (int i0 = sl; i0 < nvalid; i0 += kEpiBatch * kEpiLanes) {
+        float wb[kEpiBatch], zb[kEpiBatch][kNU];
 #pragma unroll
-        for (int j = 0; j < kNU; ++j) {
-          if (j >= nu) break;
-          const float u = clampf(Uk[j] + d.sigma[j] * zz[j], d.u_min[j], d.u_max[j]);
-          const float dv = u - Uk[j];
-          if (acc == MPPI_ACC_F64) {
-            dacc[j] = fma((double)w, (double)dv, dacc[j]);
-          } else if (acc == MPPI_ACC_F32) {
-            hi[j] = fmaf(w, dv, hi[j]);
-          } else {
-            kahan_add(hi[j], lo[j], w * dv);
+        for (int t = 0; t < kEpiBatch; ++t) {
+          const int ic = min(i0 + t * kEpiLanes, nvalid - 1);  // in range; unused past nvalid
+          wb[t] = sE[ic];
+          if (GEN == 2)
+            gen_noise<BF16, false>(d, iter, tile.m0 + ic, k, zb[t], five);
+          else
+            load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + ic, zb[t], five);
+        }
+#pragma unroll
+        for (int t = 0; t < kEpiBatch; ++t) {
+          if (i0 + t * kEpiLanes >= nvalid) break;
+          const float w = wb[t];
+#pragma unroll
+          for (int j = 0; j < kNU; ++j) {
+            if (j >= nu) break;
+            const float u = clampf(Uk[j] + d.sigma[j] * zb[t][j], d.u_min[j], d.u_max[j]);
+            const float dv = u - Uk[j];
+            if (acc == MPPI_ACC_F64) {
+              dacc[j] = fma((double)w, (double)dv, dacc[j]);
+            } else if (acc == MPPI_ACC_F32) {
+              hi[j] = fmaf(w, dv, hi[j]);
+            } else {
+              kahan_add(hi[j], lo[j], w * dv);
+            }
           }
         }
       }
