@@ -475,7 +475,7 @@ int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; 
 #endif
 static_assert(MPPI_EPI_BATCH >= 1 && MPPI_EPI_BATCH <= 16, "MPPI_EPI_BATCH must be in [1, 16]");
 #ifndef MPPI_EPI_LANES
-#define MPPI_EPI_LANES 8
+#define MPPI_EPI_LANES 4
 #endif
 static_assert(MPPI_EPI_LANES >= 1 && MPPI_EPI_LANES <= 32 && (MPPI_EPI_LANES & (MPPI_EPI_LANES - 1)) == 0,
               "MPPI_EPI_LANES must be a power of two in [1, 32]");
