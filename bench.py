@@ -398,7 +398,7 @@ def main():
                     for it in items]
 
         tuning = AT.tune_batch(make_handles, X0, t0, blocks=(64, 96, 128), modes=(1, 2), cache=None,
-                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN), spts=(1, 2))
+                               noise_gens=(M.NOISEGEN_KERNEL, M.NOISEGEN_FUSED, M.NOISEGEN_REGEN), spts=(1, 2, 4))
     ctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track, block=tuning["block"], noise_gen=tuning["noise_gen"],
                          spt=tuning["spt"]) for it in items]
     hs = [c.h for c in ctls]
@@ -522,16 +522,21 @@ def main():
     # ---- plain path: one solve per launch sequence ----
     plain = None
     if not args.no_plain and rank == 0:
-        # the same 256 solves, one mppi_solve call each
+        # the same 256 solves, one mppi_solve call each, on handles with the
+        # single-solve launch shape (one sample per thread: the batch's tuned
+        # shape can be slower for a solve launched alone)
+        pctls = [M.Controller(W.ModelConfig(), make_cfg(it), it.track) for it in items]
         lat_p = []
-        for c, x in zip(ctls, X0):
+        for c, x in zip(pctls, X0):
             c.solve(x, t0)
         tt = time.perf_counter()
-        for c, x in zip(ctls, X0):
+        for c, x in zip(pctls, X0):
             t = time.perf_counter()
             c.solve(x, t0)
             lat_p.append(time.perf_counter() - t)
         wall = time.perf_counter() - tt
+        for c in pctls:
+            c.close()
         plain = {"batch_one_solve_per_launch": {
             "value": steps_per_solve / wall, "unit": "rollout-steps/s", "solves_per_s": len(items) / wall,
             "p50_ms": float(np.percentile(lat_p, 50) * 1e3), "p99_ms": float(np.percentile(lat_p, 99) * 1e3)}}
