@@ -2,8 +2,9 @@
 //
 //   noise_kernel     Eq. 3: Philox4x32-10 -> Box-Muller standard normals,
 //                    stored [N][K] so that a warp writes 512 contiguous bytes.
-//   rollout_kernel   Eq. 2 + Eq. 6-9: one thread per sample, RK4 in registers,
-//                    objective and feasibility penalty per step; then Eq. 4/5
+//   rollout_kernel   Eq. 2 + Eq. 6-9: a thread rolls out one sample at a time
+//                    (one or more per thread), RK4 in registers, objective and
+//                    feasibility penalty per step; then Eq. 4/5
 //                    in flash-softmax form: each block reduces its samples to
 //                    (local min cost, sum of exp weights, weighted deviation
 //                    sums per (step, input)) and the last block of a group /
