@@ -451,10 +451,12 @@ def test_batch_mixing_variants_equals_alone(M, use_graph):
         g2.close()
 
 
-def test_full_bench_batch_sampled_against_oracle(O, M):
+@pytest.mark.parametrize("spt", [1, 2])
+def test_full_bench_batch_sampled_against_oracle(O, M, spt):
     """The bench's own workload and launch: the 256-drone uneven batch (K
     log-uniform in [1024, 16384], N in [20, 80], 1/3 each objective), solved
-    once through a captured batch plan with concurrent branches.  Sampled
+    once through a captured batch plan with concurrent branches, at one and at
+    two samples per thread (the autotuned launch shape).  Sampled
     solves -- the first two of each objective, the largest K and the longest
     N -- against the oracle on the same inputs.  The nominal tolerance takes
     the measured cost error of the weighted samples (long horizons and large
@@ -469,7 +471,7 @@ def test_full_bench_batch_sampled_against_oracle(O, M):
             x = it.track.ref[int(round(t0 / it.track.dt_ref)) % it.track.ref.shape[0]].copy()
         case = f32_case(W.ModelConfig(), sc, it.track, x)
         cases.append(case)
-        ctls.append(M.Controller(case.mc, case.sc, case.tr))
+        ctls.append(M.Controller(case.mc, case.sc, case.tr, spt=spt))
         X0.append(case.x0)
     plan = M.mppi_batch_create([c.h for c in ctls], use_graph=1)
     M.mppi_batch_solve(plan, len(items), np.array(X0), np.full(len(items), t0))
