@@ -87,6 +87,17 @@ def test_error_paths_need_no_device(lib_path):
     assert b"samples_per_thread" in L.mppi_last_error()
     assert L.mppi_solve(None, None, 0.0, None, None) == mppi.MPPI_ERR_ARG
     assert L.mppi_destroy(None) == 0
+    # empty and malformed batches are refused before any device work
+    b = ctypes.c_void_p()
+    hs = (ctypes.c_void_p * 2)()
+    assert L.mppi_batch_create(0, hs, 1, ctypes.byref(b)) == mppi.MPPI_ERR_ARG
+    assert L.mppi_batch_create(2, hs, 1, ctypes.byref(b)) == mppi.MPPI_ERR_ARG  # null handles
+    assert b"null handle" in L.mppi_last_error()
+    x = (ctypes.c_float * 13)()
+    t = (ctypes.c_double * 1)()
+    u = (ctypes.c_float * 5)()
+    assert L.mppi_solve_batch(0, hs, x, t, None, u) == mppi.MPPI_ERR_ARG
+    assert L.mppi_batch_destroy(None) == 0
 
 
 def test_product_path_does_not_touch_the_oracle():
