@@ -413,7 +413,7 @@ int mppi_default_params(mppi_params_t* p, int32_t objective, int32_t K, int32_t 
   const float sg[5] = {(float)(0.3 * 0.85 * 9.81), 1.f, 1.f, 1.f, 5.f};
   for (int i = 0; i < 5; ++i) p->sigma[i] = sg[i];
   p->w_limit = 1000.f;
-  p->q_near = 0.1f;
+  p->q_near = 0.05f;
   p->r_near = 1.5f;
   p->temporal_rule = MPPI_RULE_TIME_ALIGNED;
   p->q_lag = 1.f;

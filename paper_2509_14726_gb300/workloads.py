@@ -80,7 +80,7 @@ class SolveConfig:
     seed: int = 0
     drone_id: int = 0
     w_limit: float = 1.0e3
-    q_near: float = 0.1
+    q_near: float = 0.05
     r_near: float = 1.5
     temporal_rule: int = 1
     q_lag: float = 1.0
