@@ -11,7 +11,8 @@ the launching stream) over the knobs the kernels expose:
   (stored), or inside the rollout and again in the update (never stored:
   no noise memory); the same draws in every form;
 * samples per thread (a block covers block x spt samples, fewer blocks per
-  solve), searched on the best of the knobs above;
+  solve), searched for every block size with the best graph form and noise
+  generation;
 * optionally the noise storage (float32 or bfloat16; bfloat16 changes the
   numerics, so it is only searched when the caller allows it).
 
@@ -163,7 +164,8 @@ def tune_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float,
     for a batch; make_handles(block) builds the batch's Controllers with that
     block size (make_handles(block, noise_gen=g) when noise_gens is given,
     make_handles(block, ..., spt=s) for the samples-per-thread stage).  The
-    samples per thread are searched on the best configuration of the others."""
+    samples per thread are searched for every block size, with the best graph
+    form and noise generation of the first stage."""
     full_key = f"{gpu_name()}|batch|{key}" if key else None
     if cache is not None and full_key and cache.get(full_key):
         return cache.get(full_key)
@@ -175,13 +177,15 @@ def tune_batch(make_handles: Callable[..., List], x0s: np.ndarray, t0: float,
                 table.append({"block": b, "graph_mode": m, "noise_gen": M.NOISEGEN_DEFAULT if g is None else g,
                               "spt": 1, "ms": time_batch(make_handles, x0s, t0, m, b, noise_gen=g)})
     best = min(table, key=lambda r: r["ms"])
+    # samples per thread: each block size, with the best graph form and noise generation
     for s in spts:
         if s == 1:
             continue
         g = None if noise_gens is None else best["noise_gen"]
-        table.append({"block": best["block"], "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
-                      "spt": s, "ms": time_batch(make_handles, x0s, t0, best["graph_mode"], best["block"],
-                                                 noise_gen=g, spt=s)})
+        for b in blocks:
+            table.append({"block": b, "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
+                          "spt": s, "ms": time_batch(make_handles, x0s, t0, best["graph_mode"], b,
+                                                     noise_gen=g, spt=s)})
     best = min(table, key=lambda r: r["ms"])
     out = {"block": best["block"], "graph_mode": best["graph_mode"], "noise_gen": best["noise_gen"],
            "spt": best["spt"], "ms": best["ms"], "table": table}

@@ -48,6 +48,6 @@ def test_tune_batch_searches_samples_per_thread():
     out = AT.tune_batch(make_handles, X0, 0.3, blocks=(64, 128), modes=(1,), spts=(1, 2, 4),
                         noise_gens=(M.NOISEGEN_KERNEL,))
     spts = sorted(r["spt"] for r in out["table"])
-    assert spts == [1, 1, 2, 4]
+    assert spts == [1, 1, 2, 2, 4, 4]  # (2 blocks at spt 1) + each block at spt 2 and 4
     best = min(out["table"], key=lambda r: r["ms"])
     assert (out["block"], out["spt"], out["ms"]) == (best["block"], best["spt"], best["ms"])
