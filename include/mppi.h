@@ -24,7 +24,10 @@
  * Errors.  Every call returns an mppi_status; nothing throws across the ABI.
  * mppi_last_error() returns a thread-local message for the last failure.
  * A handle is not thread-safe: calls on one handle must be serialised by the
- * caller (different handles may be used from different threads).
+ * caller (different handles may be used from different threads).  The same
+ * holds for an explicit batch plan (mppi_batch_*) and for the handles it
+ * holds; mppi_solve_batch's internal plan cache is safe to call from several
+ * threads.
  *
  * Ownership.  mppi_create deep-copies model, params and track into device
  * memory owned by the handle; the caller keeps ownership of everything it
