@@ -154,6 +154,10 @@ struct mppi_batch_s {
   std::vector<NGroup> noise_groups;
   int32_t* d_which = nullptr;
   int n_which = 0;
+  // captured form: the rollout group (branch) that holds every gate-progress
+  // solve runs the nominal rollouts right after its own rollout, so that they
+  // overlap the other branches instead of following the join (-1: after it)
+  int nominal_branch = -1;
   void* dev = nullptr;
   HostIO io;
   bool use_graph = false;
@@ -911,6 +915,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     if (g.gen == MPPI_NOISEGEN_KERNEL)
       CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs, g.nom));
     CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen, g.rot));
+    if (i == b->nominal_branch) CU(launch_nominal(b->d_descs, b->d_which, b->n_which, bs));
     CU(cudaEventRecord(b->join[i], bs));
     CU(cudaStreamWaitEvent(s, b->join[i], 0));
   }
@@ -930,7 +935,8 @@ static int capture_dev_graph(mppi_batch b, const float* x0, const double* t0, fl
   if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "begin capture failed");
   const int rc = batch_enqueue_branches(b, iod, b->cap_stream);
-  const cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
+  const cudaError_t e2 =
+      b->nominal_branch < 0 ? launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream) : cudaSuccess;
   cudaGraph_t graph = nullptr;
   const cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
   if (rc || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -1106,6 +1112,13 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
         if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
           return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
       }
+      int gate_groups = 0, gate_at = -1;
+      for (int i = 0; i < G; ++i)
+        if (b->rollout_groups[i].objective == MPPI_OBJ_GATE) {
+          ++gate_groups;
+          gate_at = i;
+        }
+      if (gate_groups == 1 && b->n_which > 0) b->nominal_branch = gate_at;
     }
     LaunchIO io;
     memset(&io, 0, sizeof io);
@@ -1117,7 +1130,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
       return cleanup(fail(MPPI_ERR_CUDA, "begin capture failed"));
     int rc2 = batch_enqueue_branches(b, io, b->cap_stream);
     cudaError_t e1 = cudaEventRecordWithFlags(b->ev, b->cap_stream, cudaEventRecordExternal);
-    cudaError_t e2 = launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream);
+    cudaError_t e2 =
+        b->nominal_branch < 0 ? launch_nominal(b->d_descs, b->d_which, b->n_which, b->cap_stream) : cudaSuccess;
     cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
     if (rc2 || e1 || e2 || e3)
       return cleanup(fail(MPPI_ERR_CUDA, "graph capture failed (%s / %s / %s)", cudaGetErrorString(e1),
