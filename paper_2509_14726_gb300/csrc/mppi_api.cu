@@ -903,7 +903,9 @@ static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s);
 
 // Captured form: every rollout group gets its own branch (its own noise
 // launch, then its rollout launch), so the groups' kernels overlap and fill
-// each other's tails; the branches join before the nominal rollout.
+// each other's tails.  The nominal rollouts run at the end of the branch that
+// holds every gate-progress solve when there is one such branch, else after
+// the branches join.
 static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
   const int G = (int)b->rollout_groups.size();
   if (G <= 1 || (int)b->branch_streams.size() < G) return batch_enqueue(b, io, s);
