@@ -612,7 +612,7 @@ def main():
             "config": {"workload": f"batched uneven MPPI solves: {len(items)} drones per GPU, K logU[1024,16384], "
                                    f"N U[20,80], dt 0.02, 5-9 gate courses, objectives 1/3 each, one CUDA graph",
                        "rollout_steps_per_step": steps_per_solve, "solves_per_step": len(items),
-                       "l2": "working set (noise 16-20 B per rollout step, ~1.1 GB) larger than the 129 MB L2",
+                       "l2": "working set (noise 16-20 B per rollout step, ~1.3 GB at 256 drones) larger than the 129 MB L2",
                        "parallelism": f"dp{world} (drones sharded, no collective)"},
             "solves_per_s": len(items) * world / (ms_max / 1e3),
             "gpu_launches": int(launches),
