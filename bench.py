@@ -3,20 +3,29 @@
 Workload (one "step"): one batched MPPI solve of 256 independent drones, each
 on its own seeded 5-9 gate course, K log-uniform in [1024, 16384], N uniform
 in [20, 80], dt = 0.02 s, objectives 1/3 each (gate progress, contouring,
-tracking), launched as one CUDA graph (noise -> rollout+cost+weights+update
--> nominal rollout).  Metric: rollout-steps/s = sum_i K_i N_i / step time.
+tracking), launched as one CUDA graph (one branch per objective: noise ->
+rollout+cost+weights+update, and the nominal rollouts at the end of the gate
+branch).  The launch shape (block size, graph form, where the normals are
+drawn, samples per thread) is autotuned first, untimed.  Metric:
+rollout-steps/s = sum_i K_i N_i / step time.
 
-  value       device-timed (CUDA events on the launch stream), inputs resident
-              in HBM (mppi_batch_solve_async on device buffers)
+  value       device-timed (CUDA events on the launch stream) over --steps
+              steps after an untimed busy phase, inputs resident in HBM
+              (mppi_batch_solve_async on device buffers)
   e2e         the public host call mppi_batch_solve: x0/t0 from host memory,
               u0 back to host memory, inside the timed region
   plain       the same 256 solves through mppi_solve one drone at a time
-              (one solve per launch sequence), and the single-drone
-              K=4096/N=50 solve: solves/s and p50/p99 latency
+              (one solve per launch sequence, single-solve launch shape), the
+              single-drone K=4096/N=50 solve and the paper's Table I sizes:
+              solves/s and p50/p99 latency
   roofline    the rollout kernels (dominant): algorithmic FP32 operations
               per launch / mean launch time, against the FP32 pipe peak
               SMs x 128 lanes x 2 x max SM clock
-  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload, and
+              the error of fresh CUDA solves of the first sampled drones
+              against it (parity_vs_oracle)
+  also        the rotor-thrust-rate model on the same batch, the closed-loop
+              objective comparison, and a served fleet (continuous batching)
 
 With torchrun (N > 1) every rank solves its own 256 drones (weak scaling, no
 collective on the data path); value = all ranks' rollout steps / max time.
