@@ -1,6 +1,7 @@
-"""The serving fleet's request schedule (CPU): Poisson-jittered arrivals at
-each drone's rate class, time-ordered, reproducible from the seed, with K and N
-drawn from the configured choices."""
+"""Host-side serving and tuning logic (CPU): the fleet's request schedule
+(Poisson-jittered arrivals at each drone's rate class, time-ordered,
+reproducible from the seed, with K and N drawn from the configured choices)
+and the autotuner's JSON cache."""
 import numpy as np
 
 from paper_2509_14726_gb300 import serving as SV, workloads as W
@@ -48,3 +49,17 @@ def test_schedule_is_reproducible_and_uses_the_choices():
     assert set(np.unique(a.K)) <= {1024, 4096, 16384}
     assert set(np.unique(a.N)) <= {30, 50, 80}
     assert len(np.unique(a.K)) == 3 and len(np.unique(a.N)) == 3
+
+
+def test_autotune_cache_round_trip_and_corrupt_file(tmp_path):
+    """The autotuner's JSON cache (no device): entries persist across
+    instances, and an unreadable file starts an empty cache."""
+    from paper_2509_14726_gb300 import autotune as AT
+    path = str(tmp_path / "sub" / "tune.json")
+    c = AT.Cache(path)
+    assert c.get("k") is None
+    c.put("k", {"block": 128, "spt": 2})
+    assert AT.Cache(path).get("k") == {"block": 128, "spt": 2}
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert AT.Cache(path).get("k") is None
