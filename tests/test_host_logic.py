@@ -1,7 +1,7 @@
 """Host-side serving and tuning logic (CPU): the fleet's request schedule
 (Poisson-jittered arrivals at each drone's rate class, time-ordered,
 reproducible from the seed, with K and N drawn from the configured choices)
-and the autotuner's JSON cache."""
+the autotuner's JSON cache and the lap counter of the closed-loop flights."""
 import numpy as np
 
 from paper_2509_14726_gb300 import serving as SV, workloads as W
@@ -63,3 +63,23 @@ def test_autotune_cache_round_trip_and_corrupt_file(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert AT.Cache(path).get("k") is None
+
+
+def test_closed_loop_gate_crossing_rule():
+    """closed_loop.crossing (the lap counter of the comparison flights):
+    front-to-back through the opening counts, at the interpolated point;
+    outside the opening, backwards, or not reaching the plane does not."""
+    from paper_2509_14726_gb300 import closed_loop as CL
+    # gate at the origin facing +x (yaw 0), half-width 0.75, half-height 0.75
+    g = np.array([0.0, 0.0, 2.0, 0.0, 0.75, 0.75])
+    a = CL.crossing(g, np.array([-1.0, 0.2, 2.1]), np.array([3.0, 0.2, 2.1]))
+    assert a is not None and abs(a - 0.25) < 1e-12
+    assert CL.crossing(g, np.array([-1.0, 0.0, 2.0]), np.array([0.0, 0.0, 2.0])) == 1.0  # s = 0 counts
+    assert CL.crossing(g, np.array([-1.0, 0.9, 2.0]), np.array([1.0, 0.9, 2.0])) is None  # beside the opening
+    assert CL.crossing(g, np.array([-1.0, 0.0, 2.9]), np.array([1.0, 0.0, 2.9])) is None  # above it
+    assert CL.crossing(g, np.array([1.0, 0.0, 2.0]), np.array([-1.0, 0.0, 2.0])) is None  # backwards
+    assert CL.crossing(g, np.array([-2.0, 0.0, 2.0]), np.array([-1.0, 0.0, 2.0])) is None  # short of the plane
+    # a yawed gate: normal along +y
+    g90 = np.array([5.0, 5.0, 2.0, np.pi / 2, 0.75, 0.75])
+    assert CL.crossing(g90, np.array([5.3, 4.0, 2.0]), np.array([5.3, 6.0, 2.0])) is not None
+    assert CL.crossing(g90, np.array([6.0, 4.0, 2.0]), np.array([6.0, 6.0, 2.0])) is None
