@@ -1,7 +1,7 @@
 """Host-side serving and tuning logic (CPU): the fleet's request schedule
 (Poisson-jittered arrivals at each drone's rate class, time-ordered,
-reproducible from the seed, with K and N drawn from the configured choices)
-the autotuner's JSON cache and the lap counter of the closed-loop flights."""
+reproducible from the seed, with K and N drawn from the configured choices),
+the autotuner's JSON cache, and the lap counter of the closed-loop flights."""
 import numpy as np
 
 from paper_2509_14726_gb300 import serving as SV, workloads as W
