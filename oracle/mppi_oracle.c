@@ -151,6 +151,7 @@ typedef struct {
                          cost perturbation moves each control (conditioning) */
   int32_t gate_at_start; /* gate index after the plant-crossing check */
   int32_t status;     /* 0 ok, 1 every cost non-finite (nominal kept) */
+  double* Us;         /* [K][N][5] the clamped sampled sequences U^m (Eq. 3) */
 } or_out;
 
 /* ---------------------------------------------------------------------- */
@@ -638,6 +639,9 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
   /* Eq. 3: sampled sequences, clamped to the input box */
   double* Us = (double*)malloc(sizeof(double) * (size_t)OR_NU * N * K);
   double* J = (double*)malloc(sizeof(double) * K);
+  /* the samples are independent: a build with OpenMP (the timing baseline
+   * on all host cores) runs them in parallel; the plain build ignores this */
+#pragma omp parallel for schedule(dynamic, 16)
   for (int32_t m = 0; m < K; ++m) {
     for (int32_t k = 0; k < N; ++k) {
       double z[5] = {0, 0, 0, 0, 0};
@@ -662,6 +666,7 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
         else u[j] = 0.0;
       }
     }
+    if (out && out->Us) memcpy(out->Us + (size_t)m * N * OR_NU, Us + (size_t)m * N * OR_NU, sizeof(double) * OR_NU * N);
     /* rollout and objective for this sample (Algorithm 1 inner loop) */
     double jabs;
     int32_t np, fp, fl;
@@ -756,6 +761,14 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
   free(Unom); free(xref); free(Us); free(J); free(w); free(Unew); free(pc); free(Xn);
   return status;
 }
+
+/* Threads the sample loop of or_solve uses (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+int or_threads(void) { return 1; }
+#endif
 
 /* Plain rollout of a given sequence (no sampling), for the model tests. */
 double or_rollout(const or_model* md, const or_params* pr, const or_track* tr, const double x0[13],

@@ -54,25 +54,29 @@ class OrState(C.Structure):
 class OrOut(C.Structure):
     _fields_ = [("Z_in", PD), ("Z", PD), ("J", PD), ("Jabs", PD), ("npass", PI), ("first_pass", PI),
                 ("near_flag", PI), ("w", PD), ("Unew", PD), ("u0", PD), ("passcnt", PI), ("theta0", PD),
-                ("xref", PD), ("Xnom", PD), ("sens", PD), ("gate_at_start", I32), ("status", I32)]
+                ("xref", PD), ("Xnom", PD), ("sens", PD), ("gate_at_start", I32), ("status", I32), ("Us", PD)]
 
 
-_lib = None
+LIB_OMP_PATH = os.path.join(HERE, "liboracle_omp.so")
+
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, -O2, no vector intrinsics)."""
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC_PATH):
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", LIB_PATH, SRC_PATH, "-lm"])
-    return LIB_PATH
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, -O2, no vector intrinsics).
+    omp: the same source with OpenMP over the samples of a solve, used only to
+    time the oracle on all host cores (the parity checks use the plain build)."""
+    path = LIB_OMP_PATH if omp else LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(SRC_PATH):
+        extra = ["-fopenmp"] if omp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", *extra,
+                               "-o", path, SRC_PATH, "-lm"])
+    return path
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = C.CDLL(LIB_PATH)
+def lib(omp: bool = False):
+    if omp not in _libs:
+        L = C.CDLL(build(omp=omp))
         L.or_philox4x32_10.argtypes = [C.POINTER(U32), C.POINTER(U32), C.POINTER(U32)]
         L.or_uniform.argtypes = [U32]
         L.or_uniform.restype = D
@@ -97,8 +101,14 @@ def lib():
         L.or_rotor_at.argtypes = [C.POINTER(OrModel), PD, PD, D, PD]
         L.or_rk4_step_rotor.argtypes = [C.POINTER(OrModel), PD, PD, PD, D, C.c_int, PD, PD]
         L.or_rollout.restype = D
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the sample loop of a solve runs on."""
+    return int(lib(omp).or_threads())
 
 
 def _pd(a: np.ndarray):
@@ -310,8 +320,9 @@ class OracleController:
     as the CUDA library's handle: nominal U*, Philox iteration, gate index,
     pass counts of the previous nominal, last x0, progress state, last thrust."""
 
-    def __init__(self, mc, sc, track, cap: Optional[int] = None):
+    def __init__(self, mc, sc, track, cap: Optional[int] = None, omp: bool = False):
         self.mc, self.sc, self.track = mc, sc, track
+        self.omp = omp
         self.m, self.p = make_model(mc), make_params(sc)
         self.tv = TrackView(track)
         self.cap = int(cap or sc.N)
@@ -358,8 +369,13 @@ class OracleController:
         if c_last is not None:
             st.c_last = float(c_last)
 
-    def solve(self, x0, t0: float = 0.0, Z_in: Optional[np.ndarray] = None, want_Z: bool = False) -> dict:
+    def solve(self, x0, t0: float = 0.0, Z_in: Optional[np.ndarray] = None, want_Z: bool = False,
+              want_Us: Optional[bool] = None) -> dict:
+        """One solve; want_Us (default: when K N <= 4e6) also returns the
+        clamped sampled sequences as "Us" [K][N][5]."""
         K, N = self.sc.K, self.sc.N
+        if want_Us is None:
+            want_Us = K * N <= 4_000_000
         x0 = _f64(x0)
         o = OrOut()
         res = {
@@ -372,6 +388,9 @@ class OracleController:
         if want_Z:
             res["Z"] = np.zeros((N, K, 5))
             o.Z = _pd(res["Z"])
+        if want_Us:
+            res["Us"] = np.zeros((K, N, 5))
+            o.Us = _pd(res["Us"])
         zin = None
         if Z_in is not None:
             zin = _f64(Z_in)
@@ -381,7 +400,7 @@ class OracleController:
         o.Unew, o.u0, o.passcnt = _pd(res["Unew"]), _pd(res["u0"]), _pi(res["passcnt"])
         o.theta0, o.xref, o.Xnom = _pd(res["theta0"]), _pd(res["xref"]), _pd(res["Xnom"])
         o.sens = _pd(res["sens"])
-        rc = lib().or_solve(C.byref(self.m), C.byref(self.p), C.byref(self.tv.c), C.byref(self.st), _pd(x0),
+        rc = lib(self.omp).or_solve(C.byref(self.m), C.byref(self.p), C.byref(self.tv.c), C.byref(self.st), _pd(x0),
                             float(t0), C.byref(o))
         if rc < 0:
             raise ValueError("oracle solve rejected its arguments")

@@ -274,7 +274,32 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
 
 }  // namespace
 
+// x as a (hi, lo) binary32 pair
+static void split_pair(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// The RK4 weights h/6, h^2/6, h/12, the low part of 1/m and the rotor torque
+// factors as (hi, lo) pairs, computed here in double (see StepConsts).
+void mppi::fill_step_consts(const mppi_model_t& m, float dt, SolveDesc& d) {
+  const double h = (double)dt;
+  float a, b, c, e, f, g;
+  split_pair(h / 6.0, a, b);
+  split_pair(h * h / 6.0, c, e);
+  split_pair(h / 12.0, f, g);
+  d.stepc.c[0] = make_float4(a, b, c, e);
+  float im, iml;
+  split_pair(1.0 / (double)m.mass, im, iml);
+  d.stepc.c[1] = make_float4(f, g, iml, 0.f);
+  const double arm2 = (double)m.arm / sqrt(2.0);
+  split_pair(arm2 / (double)m.inertia[0], d.kt[0][0], d.kt[0][1]);
+  split_pair(arm2 / (double)m.inertia[1], d.kt[1][0], d.kt[1][1]);
+  split_pair((double)m.c_tau / (double)m.inertia[2], d.kt[2][0], d.kt[2][1]);
+}
+
 void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int nu, SolveDesc& d) {
+  fill_step_consts(m, p.dt, d);
   d.mass = m.mass;
   d.inv_mass = (float)(1.0 / (double)m.mass);
   d.gravity = m.gravity;
@@ -877,6 +902,7 @@ static int rollout_states_impl(const mppi_model_t* model, float dt, int32_t N, i
   md.gyro[2] = (float)((Jy - Jx) / Jz);
   for (int i = 0; i < 3; ++i) md.drag[i] = model->drag[i];
   md.has_drag = (model->drag[0] != 0.f || model->drag[1] != 0.f || model->drag[2] != 0.f) ? 1 : 0;
+  fill_step_consts(*model, dt, md);
   CU(launch_rollout_states(md, dt, N, B, d_x0, d_U, d_X, static_cast<cudaStream_t>(stream), d_T0, d_T));
   return MPPI_OK;
 }

@@ -45,10 +45,21 @@ struct DevState {
   int32_t pad_;
 };
 
+// Step constants as (hi, lo) binary32 pairs, so that the RK4 weights h/6,
+// h^2/6, h/12 and the factor 1/m carry no systematic rounding bias (a bias
+// of a constant factor integrates linearly over the horizon, where random
+// rounding only random-walks):
+//   c[0] = (h/6, lo, h^2/6, lo), c[1] = (h/12, lo, 1/m lo part, 0).
+// Kept in shared memory and read where used.
+struct StepConsts {
+  float4 c[2];
+};
+
 // --------------------------------------------------------------------------
 // per-handle solve descriptor (device memory, read by every block)
 // --------------------------------------------------------------------------
 struct SolveDesc {
+  StepConsts stepc;     // RK4 weights and 1/m as (hi, lo) pairs (first: 16-byte aligned)
   // model (Eq. 2, CTBR input)
   float mass, inv_mass, gravity, k_omega;
   float gyro[3];        // (Jz-Jy)/Jx, (Jx-Jz)/Jy, (Jy-Jx)/Jz
@@ -104,6 +115,7 @@ struct SolveDesc {
   // rotor-thrust-rate model (model kind MPPI_MODEL_ROTOR_RATE)
   int32_t rotor;
   float arm2, c_tau, thrust_min, thrust_max, inv_J[3];
+  float kt[3][2];       // torque factors l/sqrt2/Jx, l/sqrt2/Jy, c_tau/Jz as (hi, lo)
   int32_t spt;          // samples per thread: a tile holds block x spt samples
 };
 
@@ -196,14 +208,93 @@ __device__ __forceinline__ uint64_t global_ns() {
 struct Quad {
   float px, py, pz, cpx, cpy, cpz;  // position + Kahan compensation
   float vx, vy, vz, cvx, cvy, cvz;  // velocity + Kahan compensation
-  float qw, qx, qy, qz;
+  float qw, qx, qy, qz;             // attitude
+  float cqw, cqx, cqy, cqz;         // its Kahan compensation (true q = q - cq)
   float wx, wy, wz;
+  float cwx, cwy, cwz;              // body-rate compensation (rotor model only)
 };
 
 struct ModelRegs {
   float inv_mass, gravity, k_omega, g0, g1, g2, d0, d1, d2;
   int has_drag;
 };
+
+// |q|^2 - 1 for a quaternion whose norm is 1 up to binary32 rounding: exact
+// products (FMA) and error-free sums, so that the result is accurate to
+// about 1e-14 instead of one rounding of |q|^2 (6e-8).
+__device__ __forceinline__ float quat_norm_excess(float w, float x, float y, float z) {
+  float s = w * w;
+  float e = fmaf(w, w, -s);
+  const float v[3] = {x, y, z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float p = v[i] * v[i];
+    const float pe = fmaf(v[i], v[i], -p);
+    const float t = s + p;
+    const float bb = t - s;
+    e += ((s - (t - bb)) + (p - bb)) + pe;
+    s = t;
+  }
+  return (s - 1.f) + e;
+}
+
+// A shared-memory vector load the compiler keeps where it is written (not
+// hoisted out of a loop into registers).
+__device__ __forceinline__ float4 lds4_volatile(const float4* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+// a state from the 13 floats of x0
+__device__ __forceinline__ void quad_init(Quad& s, const float* x0) {
+  s.px = x0[0]; s.py = x0[1]; s.pz = x0[2];
+  s.cpx = s.cpy = s.cpz = 0.f;
+  s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5];
+  s.cvx = s.cvy = s.cvz = 0.f;
+  s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
+  s.cqw = s.cqx = s.cqy = s.cqz = 0.f;
+  s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
+  s.cwx = s.cwy = s.cwz = 0.f;
+}
+
+// c/m from the pair (inv_mass, lo): the correctly rounded product instead of
+// c * round(1/m), whose bias is the same on every step
+__device__ __forceinline__ float thrust_accel(float c, float inv_mass, float inv_mass_lo) {
+  const float a = c * inv_mass;
+  return a + fmaf(c, inv_mass_lo, fmaf(c, inv_mass, -a));
+}
+
+// The RK4 combination of the attitude: q <- (q + D) / |q + D| with
+// D = h/12 (k1 + 2 k2 + 2 k3 + k4) of the doubled quaternion rate.  With
+// |q|^2 = 1 + qe, delta = |q + D|^2 - 1 = qe + 2 q.D + |D|^2: both terms are
+// small (D is nearly orthogonal to q), so delta is accurate in binary32, and
+// 1/sqrt(1 + delta) - 1 = -delta/2 + 3 delta^2/8 - ...  The renormalised
+// increment D + (q + D) e goes into the compensated q with one Kahan step per
+// component; no component is rounded back to binary32.
+// qe: |q|^2 - 1 before the step (quat_norm_excess of x0's quaternion on the
+// first step; 0 afterwards, since every step leaves |q| = 1).
+__device__ __forceinline__ void quat_advance(Quad& s, float qe, float Dw, float Dx, float Dy, float Dz) {
+  const float qd = s.qw * Dw + s.qx * Dx + s.qy * Dy + s.qz * Dz;
+  const float d2 = Dw * Dw + Dx * Dx + Dy * Dy + Dz * Dz;
+  const float dd = qe + fmaf(2.f, qd, d2);
+  const float e = fabsf(dd) < 1e-3f ? dd * fmaf(0.375f, dd, -0.5f) : rsqrtf(1.f + dd) - 1.f;
+  kahan_add(s.qw, s.cqw, fmaf(s.qw + Dw, e, Dw));
+  kahan_add(s.qx, s.cqx, fmaf(s.qx + Dx, e, Dx));
+  kahan_add(s.qy, s.cqy, fmaf(s.qy + Dy, e, Dy));
+  kahan_add(s.qz, s.cqz, fmaf(s.qz + Dz, e, Dz));
+}
+
+// v += (h/6) a with the constant as a pair: the increment's product error and
+// the constant's low part go into the compensation
+__device__ __forceinline__ void vel_advance(float& v, float& cv, float a, float h6, float h6l) {
+  const float y = h6 * a;
+  const float lo = fmaf(h6l, a, fmaf(h6, a, -y));
+  kahan_add(v, cv, y);
+  cv -= lo;
+}
 
 // Body-z thrust acceleration R(q) e_z c/m - g e_z, with the factor 2 of R
 // folded into ac2 = 2 c/m and acg = c/m - g (both per step).
@@ -250,10 +341,14 @@ __device__ __forceinline__ void attitude_rate2(const ModelRegs& M, float kcx, fl
 // accumulation) to dp.  Without drag the accelerations depend on q only, so
 // the stage velocities are not formed:  p += h v + h^2/6 (a1 + a2 + a3),
 // v += h/6 (a1 + 2 a2 + 2 a3 + a4).
+// sc: the solve's StepConsts in shared memory; qe: |q|^2 - 1 at the start of
+// the step (see quat_advance).
 template <bool DRAG>
-__device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, float cx, float cy, float cz,
-                                         float h, float& dpx, float& dpy, float& dpz) {
-  const float ac = c * M.inv_mass;
+__device__ __forceinline__ void rk4_step(const ModelRegs& M, const StepConsts* sc, Quad& s, float qe, float c,
+                                         float cx, float cy, float cz, float h, float& dpx, float& dpy,
+                                         float& dpz) {
+  const float4 c1 = lds4_volatile(&sc->c[1]);
+  const float ac = thrust_accel(c, M.inv_mass, c1.z);
   const float ac2 = 2.f * ac, acg = ac - M.gravity;
   const float kcx = M.k_omega * cx, kcy = M.k_omega * cy, kcz = M.k_omega * cz;
   const float h2 = 0.5f * h, h4 = 0.25f * h;
@@ -306,26 +401,27 @@ __device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, f
   sqw += dqw; sqx += dqx; sqy += dqy; sqz += dqz;
   swx += dwx; swy += dwy; swz += dwz;
   sax += ax; say += ay; saz += az;
-  // combine
-  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6, h12 = 0.5f * h6;
-  dpx = h * s.vx + hh6 * pax;
-  dpy = h * s.vy + hh6 * pay;
-  dpz = h * s.vz + hh6 * paz;
+  // combine: p and v compensated with the weights as (hi, lo) pairs, q
+  // compensated and renormalised exactly (quat_advance), w plain (the rate
+  // loop damps its rounding)
+  const float4 c0 = lds4_volatile(&sc->c[0]);  // (h/6, lo, h^2/6, lo)
+  dpx = h * s.vx + c0.z * pax;
+  dpy = h * s.vy + c0.z * pay;
+  dpz = h * s.vz + c0.z * paz;
   kahan_add(s.px, s.cpx, dpx);
   kahan_add(s.py, s.cpy, dpy);
   kahan_add(s.pz, s.cpz, dpz);
-  kahan_add(s.vx, s.cvx, h6 * sax);
-  kahan_add(s.vy, s.cvy, h6 * say);
-  kahan_add(s.vz, s.cvz, h6 * saz);
-  const float qw1 = s.qw + h12 * sqw, qx1 = s.qx + h12 * sqx, qy1 = s.qy + h12 * sqy, qz1 = s.qz + h12 * sqz;
-  s.wx += h6 * swx;
-  s.wy += h6 * swy;
-  s.wz += h6 * swz;
-  const float rn = rsqrtf(qw1 * qw1 + qx1 * qx1 + qy1 * qy1 + qz1 * qz1);
-  s.qw = qw1 * rn;
-  s.qx = qx1 * rn;
-  s.qy = qy1 * rn;
-  s.qz = qz1 * rn;
+  s.cpx -= c0.w * pax;
+  s.cpy -= c0.w * pay;
+  s.cpz -= c0.w * paz;
+  vel_advance(s.vx, s.cvx, sax, c0.x, c0.y);
+  vel_advance(s.vy, s.cvy, say, c0.x, c0.y);
+  vel_advance(s.vz, s.cvz, saz, c0.x, c0.y);
+  s.wx += c0.x * swx;
+  s.wy += c0.x * swy;
+  s.wz += c0.x * swz;
+  quat_advance(s, qe, fmaf(c1.y, sqw, c1.x * sqw), fmaf(c1.y, sqx, c1.x * sqx), fmaf(c1.y, sqy, c1.x * sqy),
+               fmaf(c1.y, sqz, c1.x * sqz));
 }
 
 // Rotor-thrust-rate model (Eq. 2 as printed): four rotor thrusts with
@@ -333,9 +429,25 @@ __device__ __forceinline__ void rk4_step(const ModelRegs& M, Quad& s, float c, f
 // thrust = their sum; torque tau = (l/sqrt2 (T0+T1-T2-T3),
 // l/sqrt2 (-T0+T1+T2-T3), c_tau (T0-T1+T2-T3)).
 struct RotorRegs {
-  float arm2, c_tau, tmin, tmax;  // arm2 = l / sqrt(2)
-  float iJx, iJy, iJz;            // 1 / J
+  float tmin, tmax;
+  float kx, kxl, ky, kyl, kz, kzl;  // l/sqrt2/Jx, l/sqrt2/Jy, c_tau/Jz as (hi, lo) pairs
 };
+
+__host__ __device__ inline RotorRegs rotor_regs(const SolveDesc& d) {
+  RotorRegs R;
+  R.tmin = d.thrust_min;
+  R.tmax = d.thrust_max;
+  R.kx = d.kt[0][0]; R.kxl = d.kt[0][1];
+  R.ky = d.kt[1][0]; R.kyl = d.kt[1][1];
+  R.kz = d.kt[2][0]; R.kzl = d.kt[2][1];
+  return R;
+}
+
+// k * x with the constant k as a (hi, lo) pair: the correctly rounded product
+__device__ __forceinline__ float pair_mul(float k, float kl, float x) {
+  const float a = k * x;
+  return a + fmaf(kl, x, fmaf(k, x, -a));
+}
 
 // twice the quaternion rate and the body-rate derivative J^-1 tau - J^-1 (w x J w)
 // for the torque accelerations (bx, by, bz) = J^-1 tau
@@ -356,14 +468,16 @@ __device__ __forceinline__ void attitude_rate2_torque(const ModelRegs& M, float 
 // The torque combinations are formed from pairwise differences of the
 // (nearly equal) thrusts, which are exact when the two are within a factor
 // of two, instead of differences of sums, which cancel.
-__device__ __forceinline__ void rotor_forces(const ModelRegs& M, const RotorRegs& R, float t0, float t1, float t2,
-                                             float t3, float& ac2, float& acg, float& bx, float& by, float& bz) {
-  const float ac = ((t0 + t1) + (t2 + t3)) * M.inv_mass;
+__device__ __forceinline__ void rotor_forces(const ModelRegs& M, const RotorRegs& R, float iml, float t0, float t1,
+                                             float t2, float t3, float& ac2, float& acg, float& bx, float& by,
+                                             float& bz) {
+  const float ac = thrust_accel((t0 + t1) + (t2 + t3), M.inv_mass, iml);
   ac2 = 2.f * ac;
   acg = ac - M.gravity;
-  bx = R.arm2 * ((t0 - t2) + (t1 - t3)) * R.iJx;
-  by = R.arm2 * ((t1 - t0) + (t2 - t3)) * R.iJy;
-  bz = R.c_tau * ((t0 - t1) + (t2 - t3)) * R.iJz;
+  // the torque factors are constants: correctly rounded products, no bias
+  bx = pair_mul(R.kx, R.kxl, (t0 - t2) + (t1 - t3));
+  by = pair_mul(R.ky, R.kyl, (t1 - t0) + (t2 - t3));
+  bz = pair_mul(R.kz, R.kzl, (t0 - t1) + (t2 - t3));
 }
 
 // One compensated step of a saturating thrust ramp: (T, c) holds T - c, the
@@ -387,10 +501,12 @@ __device__ __forceinline__ float rotor_advance(float& T, float& c, float y, floa
 // step.  dp receives the position increment, dT2 the squared thrust change
 // sum_s (T_s(t+h) - T_s(t))^2.
 template <bool DRAG>
-__device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRegs& R, Quad& s, float T[4],
-                                               float Tc[4], float u0, float u1, float u2, float u3, float h,
-                                               float& dpx, float& dpy, float& dpz, float& dT2) {
+__device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRegs& R, const StepConsts* sc,
+                                               Quad& s, float qe, float T[4], float Tc[4], float u0, float u1,
+                                               float u2, float u3, float h, float& dpx, float& dpy, float& dpz,
+                                               float& dT2) {
   const float h2 = 0.5f * h, h4 = 0.25f * h;
+  const float iml = lds4_volatile(&sc->c[1]).z;
   const float t0 = T[0] - Tc[0], t1 = T[1] - Tc[1], t2 = T[2] - Tc[2], t3 = T[3] - Tc[3];
   const float m0 = clampf(T[0] + (u0 * h2 - Tc[0]), R.tmin, R.tmax);
   const float m1 = clampf(T[1] + (u1 * h2 - Tc[1]), R.tmin, R.tmax);
@@ -405,7 +521,7 @@ __device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRe
   float ac2, acg, bx, by, bz;
   float dqw, dqx, dqy, dqz, dwx, dwy, dwz, ax, ay, az;
   // stage 1 (start-of-step thrusts)
-  rotor_forces(M, R, t0, t1, t2, t3, ac2, acg, bx, by, bz);
+  rotor_forces(M, R, iml, t0, t1, t2, t3, ac2, acg, bx, by, bz);
   attitude_rate2_torque(M, bx, by, bz, s.qw, s.qx, s.qy, s.qz, s.wx, s.wy, s.wz, dqw, dqx, dqy, dqz, dwx, dwy, dwz);
   if (DRAG)
     accel_drag(M, ac2, acg, s.qw, s.qx, s.qy, s.qz, s.vx, s.vy, s.vz, ax, ay, az);
@@ -416,7 +532,7 @@ __device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRe
   float pax = ax, pay = ay, paz = az;
   float vx2 = 0.f, vy2 = 0.f, vz2 = 0.f;
   // stages 2 and 3 (mid-step thrusts)
-  rotor_forces(M, R, m0, m1, m2, m3, ac2, acg, bx, by, bz);
+  rotor_forces(M, R, iml, m0, m1, m2, m3, ac2, acg, bx, by, bz);
   float qw2 = s.qw + h4 * dqw, qx2 = s.qx + h4 * dqx, qy2 = s.qy + h4 * dqy, qz2 = s.qz + h4 * dqz;
   float wx2 = s.wx + h2 * dwx, wy2 = s.wy + h2 * dwy, wz2 = s.wz + h2 * dwz;
   if (DRAG) { vx2 = s.vx + h2 * ax; vy2 = s.vy + h2 * ay; vz2 = s.vz + h2 * az; }
@@ -442,7 +558,7 @@ __device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRe
   sax += 2.f * ax; say += 2.f * ay; saz += 2.f * az;
   pax += ax; pay += ay; paz += az;
   // stage 4 (end-of-step thrusts)
-  rotor_forces(M, R, e0, e1, e2, e3, ac2, acg, bx, by, bz);
+  rotor_forces(M, R, iml, e0, e1, e2, e3, ac2, acg, bx, by, bz);
   qw2 = s.qw + h2 * dqw; qx2 = s.qx + h2 * dqx; qy2 = s.qy + h2 * dqy; qz2 = s.qz + h2 * dqz;
   wx2 = s.wx + h * dwx; wy2 = s.wy + h * dwy; wz2 = s.wz + h * dwz;
   if (DRAG) { vx2 = s.vx + h * ax; vy2 = s.vy + h * ay; vz2 = s.vz + h * az; }
@@ -454,26 +570,26 @@ __device__ __forceinline__ void rk4_step_rotor(const ModelRegs& M, const RotorRe
   sqw += dqw; sqx += dqx; sqy += dqy; sqz += dqz;
   swx += dwx; swy += dwy; swz += dwz;
   sax += ax; say += ay; saz += az;
-  // combine (the same form as the collective-thrust step)
-  const float h6 = h * (1.0f / 6.0f), hh6 = h * h6, h12 = 0.5f * h6;
-  dpx = h * s.vx + hh6 * pax;
-  dpy = h * s.vy + hh6 * pay;
-  dpz = h * s.vz + hh6 * paz;
+  // combine (the collective-thrust step's form; w compensated too: this
+  // model has no rate loop, so rounding in w integrates undamped)
+  const float4 c0 = lds4_volatile(&sc->c[0]), c1 = lds4_volatile(&sc->c[1]);
+  dpx = h * s.vx + c0.z * pax;
+  dpy = h * s.vy + c0.z * pay;
+  dpz = h * s.vz + c0.z * paz;
   kahan_add(s.px, s.cpx, dpx);
   kahan_add(s.py, s.cpy, dpy);
   kahan_add(s.pz, s.cpz, dpz);
-  kahan_add(s.vx, s.cvx, h6 * sax);
-  kahan_add(s.vy, s.cvy, h6 * say);
-  kahan_add(s.vz, s.cvz, h6 * saz);
-  const float qw1 = s.qw + h12 * sqw, qx1 = s.qx + h12 * sqx, qy1 = s.qy + h12 * sqy, qz1 = s.qz + h12 * sqz;
-  s.wx += h6 * swx;
-  s.wy += h6 * swy;
-  s.wz += h6 * swz;
-  const float rn = rsqrtf(qw1 * qw1 + qx1 * qx1 + qy1 * qy1 + qz1 * qz1);
-  s.qw = qw1 * rn;
-  s.qx = qx1 * rn;
-  s.qy = qy1 * rn;
-  s.qz = qz1 * rn;
+  s.cpx -= c0.w * pax;
+  s.cpy -= c0.w * pay;
+  s.cpz -= c0.w * paz;
+  vel_advance(s.vx, s.cvx, sax, c0.x, c0.y);
+  vel_advance(s.vy, s.cvy, say, c0.x, c0.y);
+  vel_advance(s.vz, s.cvz, saz, c0.x, c0.y);
+  vel_advance(s.wx, s.cwx, swx, c0.x, c0.y);
+  vel_advance(s.wy, s.cwy, swy, c0.x, c0.y);
+  vel_advance(s.wz, s.cwz, swz, c0.x, c0.y);
+  quat_advance(s, qe, fmaf(c1.y, sqw, c1.x * sqw), fmaf(c1.y, sqx, c1.x * sqx), fmaf(c1.y, sqy, c1.x * sqy),
+               fmaf(c1.y, sqz, c1.x * sqz));
   dT2 = d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {

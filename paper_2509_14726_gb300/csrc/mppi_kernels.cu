@@ -34,16 +34,6 @@ namespace mppi {
 constexpr int kNoiseUnroll = MPPI_NOISE_UNROLL;
 constexpr int kRolloutUnroll = MPPI_ROLLOUT_UNROLL;
 
-// A shared-memory vector load the compiler keeps where it is written (not
-// hoisted out of a loop into registers).
-__device__ __forceinline__ float4 lds4_volatile(const float4* p) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"((uint32_t)__cvta_generic_to_shared(p)));
-  return v;
-}
-
 // bounded wait on an mbarrier phase; returns false after ~timeout_ns
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
@@ -227,7 +217,7 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
   L.off_path = o;
   if (objective == MPPI_OBJ_CONTOUR && path_in_smem) o += align16((uint32_t)S * 6u * 4u);
   L.off_xref = o;
-  if (objective == MPPI_OBJ_TRACK) o += align16((uint32_t)(N + 1) * kNX * 4u);
+  if (objective == MPPI_OBJ_TRACK) o += align16((uint32_t)(N + 1) * kNX * 4u) + align16((uint32_t)(N + 1) * 16u);
   L.off_e = o;
   o += align16((uint32_t)tile * 4u);
   L.off_j = o;  // the tile's costs as compensated pairs: [tile] hi, then [tile] lo
@@ -493,8 +483,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   __shared__ float4 sBnd[5];  // (sigma, u_min, u_max, 0) per input; (w_limit, omega_max, z_floor, 0)
   __shared__ int s_adv, s_last, s_group_last, s_bad;
   __shared__ double s_theta0, s_m, s_S;
-  __shared__ float s_vth0, s_f0;
-  __shared__ int s_j0;
+  __shared__ float s_vth0, s_f0, s_qe0, s_rf0;
+  __shared__ float2 s_rr;
+  __shared__ int s_j0, s_ri0;
   __shared__ float s_best_d[32];
   __shared__ int s_best_j[32];
   __shared__ float s_best_t[32];
@@ -509,6 +500,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   if (tid < kNX) x0s[tid] = io.x0 ? io.x0[(size_t)tile.solve * kNX + tid] : io.x0v[tid];
   __syncthreads();
   const SolveDesc& d = sd;
+  if (tid == 0) s_qe0 = quat_norm_excess(x0s[6], x0s[7], x0s[8], x0s[9]);
   if (tid < 4) sBnd[tid] = make_float4(d.sigma[tid], d.u_min[tid], d.u_max[tid], 0.f);
   if (tid == 4) sBnd[4] = make_float4(d.w_limit, d.omega_max, d.z_floor, 0.f);
   const int K = d.K, N = d.N, nu = d.nu, B = d.block;
@@ -520,7 +512,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   int* sPrev = reinterpret_cast<int*>(smem + Ls.off_prev);
   GateF* sG = reinterpret_cast<GateF*>(smem + Ls.off_gates);
   float* sPath = path_smem ? reinterpret_cast<float*>(smem + Ls.off_path) : nullptr;
-  float* sX = reinterpret_cast<float*>(smem + Ls.off_xref);
+  float* sX = reinterpret_cast<float*>(smem + Ls.off_xref);           // [N+1][13]
+  float* sXl = sX + align16((uint32_t)(N + 1) * kNX * 4u) / 4;          // [N+1][4] low parts of p
   float* sE = reinterpret_cast<float*>(smem + Ls.off_e);
   float* sJ = reinterpret_cast<float*>(smem + Ls.off_j);  // [TS] hi (NaN: not valid), [TS] lo
   double* sMerge = reinterpret_cast<double*>(smem + Ls.off_merge);
@@ -568,23 +561,45 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     __syncthreads();
     for (int k = tid; k < N; k += blockDim.x) sPrev[k] = max(0, d.prevcnt[k] - s_adv);
   }
-  double t0 = 0.0;
   if (OBJ == MPPI_OBJ_TRACK) {
-    t0 = io.t0 ? io.t0[tile.solve] : io.t0v;
-    // reference window x_ref(t0 + k dt), k = 0..N (linear, nlerp for q)
-    const double period = (double)d.T * (double)d.dt_ref;
-    for (int k = tid; k <= N; k += blockDim.x) {
-      double tau = fmod(t0 + (double)k * (double)d.dt, period);
+    // reference window x_ref(t0 + k dt), k = 0..N: linear in the table, nlerp
+    // for q.  The time origin becomes a table position (row i0, fraction f0)
+    // once per block; the step positions f0 + k dt/dt_ref are then formed in
+    // binary32 with dt/dt_ref as a (hi, lo) pair and exact integer parts.
+    if (tid == 0) {
+      const double t0 = io.t0 ? io.t0[tile.solve] : io.t0v;
+      const double period = (double)d.T * (double)d.dt_ref;
+      double tau = fmod(t0, period);
       if (tau < 0) tau += period;
-      const double sidx = tau / (double)d.dt_ref;
-      int i = (int)floor(sidx);
-      float f = (float)(sidx - (double)i);
-      if (i >= d.T) { i = d.T - 1; f = 1.f; }
-      const int i1 = (i + 1) % d.T;
+      const double s0 = tau / (double)d.dt_ref;
+      const double fi = floor(s0);
+      s_ri0 = (int)fi;
+      s_rf0 = (float)(s0 - fi);
+      const float r = d.dt / d.dt_ref;
+      s_rr = make_float2(r, fmaf(-r, d.dt_ref, d.dt) / d.dt_ref);
+    }
+    __syncthreads();
+    const float2 rr = s_rr;
+    for (int k = tid; k <= N; k += blockDim.x) {
+      const float kf = (float)k;
+      const float p = kf * rr.x;
+      const float pe = fmaf(kf, rr.x, -p) + kf * rr.y;
+      const float ip = floorf(p);
+      float f = ((p - ip) + pe) + s_rf0;
+      const float fl = floorf(f);
+      f -= fl;
+      int i = (s_ri0 + (int)ip + (int)fl) % d.T;
+      if (i < 0) i += d.T;
+      const int i1 = i + 1 < d.T ? i + 1 : 0;
       const float* a = d.ref + (size_t)13 * i;
       const float* b = d.ref + (size_t)13 * i1;
       float* o = sX + (size_t)13 * k;
-      for (int c = 0; c < 13; ++c) o[c] = (1.f - f) * a[c] + f * b[c];
+      float* ol = sXl + (size_t)4 * k;
+      for (int c = 0; c < 13; ++c) o[c] = fmaf(f, b[c] - a[c], a[c]);
+      // positions as (hi, lo): the error terms are then formed relative to
+      // the table row instead of to a binary32 rounding of it
+      for (int c = 0; c < 3; ++c) ol[c] = fmaf(f, b[c] - a[c], a[c] - o[c]);
+      ol[3] = 0.f;
       const float dot = a[6] * b[6] + a[7] * b[7] + a[8] * b[8] + a[9] * b[9];
       const float sg = dot < 0.f ? -1.f : 1.f;
       float n2 = 0.f;
@@ -661,9 +676,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   M.inv_mass = d.inv_mass; M.gravity = d.gravity; M.k_omega = d.k_omega;
   M.g0 = d.gyro[0]; M.g1 = d.gyro[1]; M.g2 = d.gyro[2];
   M.d0 = d.drag[0]; M.d1 = d.drag[1]; M.d2 = d.drag[2]; M.has_drag = d.has_drag;
-  RotorRegs RR;
-  RR.arm2 = d.arm2; RR.c_tau = d.c_tau; RR.tmin = d.thrust_min; RR.tmax = d.thrust_max;
-  RR.iJx = d.inv_J[0]; RR.iJy = d.inv_J[1]; RR.iJz = d.inv_J[2];
+  RotorRegs RR = rotor_regs(d);
 #pragma unroll 1
   for (int rep = 0; rep < spt; ++rep) {
     const int m = tile.m0 + tid + rep * B;
@@ -672,12 +685,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     int passed = 0, first = -1;
     if (active) {
       Quad s;
-      s.px = x0s[0]; s.py = x0s[1]; s.pz = x0s[2];
-      s.cpx = s.cpy = s.cpz = 0.f;
-      s.vx = x0s[3]; s.vy = x0s[4]; s.vz = x0s[5];
-      s.cvx = s.cvy = s.cvz = 0.f;
-      s.qw = x0s[6]; s.qx = x0s[7]; s.qy = x0s[8]; s.qz = x0s[9];
-      s.wx = x0s[10]; s.wy = x0s[11]; s.wz = x0s[12];
+      quad_init(s, x0s);
       const float h = d.dt;
       // rotor thrusts (rotor model): the controller's integrated commands
       float Tr[4] = {0.f, 0.f, 0.f, 0.f}, Trc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -743,19 +751,20 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         if (OBJ == MPPI_OBJ_TRACK) {
           // Eq. 8 stage term on x_k and u_k
           const float* xr = sX + kNX * k;
+          const float* xl = sXl + 4 * k;
           const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
           const float sg = dot < 0.f ? -1.f : 1.f;
           float e;
-          e = (s.px - xr[0]) - s.cpx; stage += d.Q[0] * e * e;
-          e = (s.py - xr[1]) - s.cpy; stage += d.Q[1] * e * e;
-          e = (s.pz - xr[2]) - s.cpz; stage += d.Q[2] * e * e;
+          e = ((s.px - xr[0]) - s.cpx) - xl[0]; stage += d.Q[0] * e * e;
+          e = ((s.py - xr[1]) - s.cpy) - xl[1]; stage += d.Q[1] * e * e;
+          e = ((s.pz - xr[2]) - s.cpz) - xl[2]; stage += d.Q[2] * e * e;
           e = (s.vx - xr[3]) - s.cvx; stage += d.Q[3] * e * e;
           e = (s.vy - xr[4]) - s.cvy; stage += d.Q[4] * e * e;
           e = (s.vz - xr[5]) - s.cvz; stage += d.Q[5] * e * e;
-          e = s.qw - sg * xr[6]; stage += d.Q[6] * e * e;
-          e = s.qx - sg * xr[7]; stage += d.Q[7] * e * e;
-          e = s.qy - sg * xr[8]; stage += d.Q[8] * e * e;
-          e = s.qz - sg * xr[9]; stage += d.Q[9] * e * e;
+          e = (s.qw - sg * xr[6]) - s.cqw; stage += d.Q[6] * e * e;
+          e = (s.qx - sg * xr[7]) - s.cqx; stage += d.Q[7] * e * e;
+          e = (s.qy - sg * xr[8]) - s.cqy; stage += d.Q[8] * e * e;
+          e = (s.qz - sg * xr[9]) - s.cqz; stage += d.Q[9] * e * e;
           e = s.wx - xr[10]; stage += d.Q[10] * e * e;
           e = s.wy - xr[11]; stage += d.Q[11] * e * e;
           e = s.wz - xr[12]; stage += d.Q[12] * e * e;
@@ -778,14 +787,14 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         float dpx, dpy, dpz;
         if (ROT) {
           if (M.has_drag)
-            rk4_step_rotor<true>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+            rk4_step_rotor<true>(M, RR, &d.stepc, s, k ? 0.f : s_qe0, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
           else
-            rk4_step_rotor<false>(M, RR, s, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
+            rk4_step_rotor<false>(M, RR, &d.stepc, s, k ? 0.f : s_qe0, Tr, Trc, u0, u1, u2, u3, h, dpx, dpy, dpz, dT2);
         } else {
           if (M.has_drag)
-            rk4_step<true>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+            rk4_step<true>(M, &d.stepc, s, k ? 0.f : s_qe0, u0, u1, u2, u3, h, dpx, dpy, dpz);
           else
-            rk4_step<false>(M, s, u0, u1, u2, u3, h, dpx, dpy, dpz);
+            rk4_step<false>(M, &d.stepc, s, k ? 0.f : s_qe0, u0, u1, u2, u3, h, dpx, dpy, dpz);
         }
         if (OBJ == MPPI_OBJ_GATE) {
           // Eq. 7: ||p_{k+1} - g||^2 - ||p_k - g||^2 = (p_{k+1} - p_k) . (p_{k+1} + p_k - 2 g),
@@ -850,19 +859,20 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         } else {
           if (k == N - 1) {
             const float* xr = sX + kNX * N;
+            const float* xl = sXl + 4 * N;
             const float dot = s.qw * xr[6] + s.qx * xr[7] + s.qy * xr[8] + s.qz * xr[9];
             const float sg = dot < 0.f ? -1.f : 1.f;
             float e;
-            e = (s.px - xr[0]) - s.cpx; stage += d.QN[0] * e * e;
-            e = (s.py - xr[1]) - s.cpy; stage += d.QN[1] * e * e;
-            e = (s.pz - xr[2]) - s.cpz; stage += d.QN[2] * e * e;
+            e = ((s.px - xr[0]) - s.cpx) - xl[0]; stage += d.QN[0] * e * e;
+            e = ((s.py - xr[1]) - s.cpy) - xl[1]; stage += d.QN[1] * e * e;
+            e = ((s.pz - xr[2]) - s.cpz) - xl[2]; stage += d.QN[2] * e * e;
             e = (s.vx - xr[3]) - s.cvx; stage += d.QN[3] * e * e;
             e = (s.vy - xr[4]) - s.cvy; stage += d.QN[4] * e * e;
             e = (s.vz - xr[5]) - s.cvz; stage += d.QN[5] * e * e;
-            e = s.qw - sg * xr[6]; stage += d.QN[6] * e * e;
-            e = s.qx - sg * xr[7]; stage += d.QN[7] * e * e;
-            e = s.qy - sg * xr[8]; stage += d.QN[8] * e * e;
-            e = s.qz - sg * xr[9]; stage += d.QN[9] * e * e;
+            e = (s.qw - sg * xr[6]) - s.cqw; stage += d.QN[6] * e * e;
+            e = (s.qx - sg * xr[7]) - s.cqx; stage += d.QN[7] * e * e;
+            e = (s.qy - sg * xr[8]) - s.cqy; stage += d.QN[8] * e * e;
+            e = (s.qz - sg * xr[9]) - s.cqz; stage += d.QN[9] * e * e;
             e = s.wx - xr[10]; stage += d.QN[10] * e * e;
             e = s.wy - xr[11]; stage += d.QN[11] * e * e;
             e = s.wz - xr[12]; stage += d.QN[12] * e * e;
@@ -1152,6 +1162,7 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
                                                       const int32_t* __restrict__ which, int n) {
   __shared__ int sPrev[4][kMaxN];
   __shared__ GateF sG[4][kMaxGates];
+  __shared__ StepConsts sSC[4];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 4 + w;
   if (i >= n) return;
@@ -1160,6 +1171,7 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
   const int N = d.N;
   const int adv = st->adv;
   for (int k = lane; k < N; k += 32) sPrev[w][k] = max(0, d.prevcnt[k] - adv);
+  if (lane < 2) sSC[w].c[lane] = d.stepc.c[lane];
   for (int g = lane; g < d.n_gates; g += 32) {
     const float* gr = d.gates + 6 * g;
     float s, c;
@@ -1175,17 +1187,13 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
     M.d0 = d.drag[0]; M.d1 = d.drag[1]; M.d2 = d.drag[2]; M.has_drag = d.has_drag;
     const float* x0 = st->prev_x0;
     Quad s;
-    s.px = x0[0]; s.py = x0[1]; s.pz = x0[2]; s.cpx = s.cpy = s.cpz = 0.f;
-    s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5]; s.cvx = s.cvy = s.cvz = 0.f;
-    s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
-    s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
+    quad_init(s, x0);
+    const float qe0 = quat_norm_excess(x0[6], x0[7], x0[8], x0[9]);
     int gi = st->gate, passed = 0;
     GateF g = load_gate(sG[w], gate_slot(gi, d.n_gates, d.closed));
     float sa = plane_dist(g, s.px, s.py);
     d.passcnt[0] = 0;
-    RotorRegs RR;
-    RR.arm2 = d.arm2; RR.c_tau = d.c_tau; RR.tmin = d.thrust_min; RR.tmax = d.thrust_max;
-    RR.iJx = d.inv_J[0]; RR.iJy = d.inv_J[1]; RR.iJz = d.inv_J[2];
+    RotorRegs RR = rotor_regs(d);
     float Tr[4] = {st->rotor_prev[0], st->rotor_prev[1], st->rotor_prev[2], st->rotor_prev[3]};
     float Trc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < N; ++k) {
@@ -1194,13 +1202,13 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
       float dpx, dpy, dpz, dT2;
       if (d.rotor) {
         if (M.has_drag)
-          rk4_step_rotor<true>(M, RR, s, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
+          rk4_step_rotor<true>(M, RR, &sSC[w], s, k ? 0.f : qe0, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
         else
-          rk4_step_rotor<false>(M, RR, s, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
+          rk4_step_rotor<false>(M, RR, &sSC[w], s, k ? 0.f : qe0, Tr, Trc, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz, dT2);
       } else if (M.has_drag) {
-        rk4_step<true>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+        rk4_step<true>(M, &sSC[w], s, k ? 0.f : qe0, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
       } else {
-        rk4_step<false>(M, s, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
+        rk4_step<false>(M, &sSC[w], s, k ? 0.f : qe0, u[0], u[1], u[2], u[3], d.dt, dpx, dpy, dpz);
       }
       const float bx = pxt(s), by = pyt(s), bz = pzt(s);
       const float sb = plane_dist(g, bx, by);
@@ -1252,10 +1260,13 @@ __global__ void normals_kernel(uint32_t seed, uint32_t drone, uint32_t k, uint32
 }
 
 // rotor (rotor model): T0 [B][4] start thrusts, Tout [B][N+1][4] thrusts
-__global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, int rotor, float dt, int N, int B,
+__global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, StepConsts SC, int rotor, float dt, int N, int B,
                                       const float* __restrict__ x0, const float* __restrict__ U,
                                       float* __restrict__ X, const float* __restrict__ T0,
                                       float* __restrict__ Tout) {
+  __shared__ StepConsts sSC;
+  if (threadIdx.x < 2) sSC.c[threadIdx.x] = SC.c[threadIdx.x];
+  __syncthreads();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   float T[4] = {0.f, 0.f, 0.f, 0.f}, Tc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1266,10 +1277,8 @@ __global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, int rotor, float
     }
   }
   Quad s;
-  s.px = x0[0]; s.py = x0[1]; s.pz = x0[2]; s.cpx = s.cpy = s.cpz = 0.f;
-  s.vx = x0[3]; s.vy = x0[4]; s.vz = x0[5]; s.cvx = s.cvy = s.cvz = 0.f;
-  s.qw = x0[6]; s.qx = x0[7]; s.qy = x0[8]; s.qz = x0[9];
-  s.wx = x0[10]; s.wy = x0[11]; s.wz = x0[12];
+  quad_init(s, x0);
+  const float qe0 = quat_norm_excess(x0[6], x0[7], x0[8], x0[9]);
   float* o = X + (size_t)b * (N + 1) * kNX;
   for (int c = 0; c < kNX; ++c) o[c] = x0[c];
   for (int k = 0; k < N; ++k) {
@@ -1277,20 +1286,20 @@ __global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, int rotor, float
     float dpx, dpy, dpz, dT2;
     if (rotor) {
       if (M.has_drag)
-        rk4_step_rotor<true>(M, R, s, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
+        rk4_step_rotor<true>(M, R, &sSC, s, k ? 0.f : qe0, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
       else
-        rk4_step_rotor<false>(M, R, s, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
+        rk4_step_rotor<false>(M, R, &sSC, s, k ? 0.f : qe0, T, Tc, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz, dT2);
       for (int c = 0; c < 4; ++c) Tout[((size_t)b * (N + 1) + k + 1) * 4 + c] = T[c] - Tc[c];
     } else if (M.has_drag) {
-      rk4_step<true>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+      rk4_step<true>(M, &sSC, s, k ? 0.f : qe0, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
     } else {
-      rk4_step<false>(M, s, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
+      rk4_step<false>(M, &sSC, s, k ? 0.f : qe0, u[0], u[1], u[2], u[3], dt, dpx, dpy, dpz);
     }
     float* r = o + (size_t)(k + 1) * kNX;
     r[0] = pxt(s); r[1] = pyt(s); r[2] = pzt(s);
     r[3] = s.vx - s.cvx; r[4] = s.vy - s.cvy; r[5] = s.vz - s.cvz;
-    r[6] = s.qw; r[7] = s.qx; r[8] = s.qy; r[9] = s.qz;
-    r[10] = s.wx; r[11] = s.wy; r[12] = s.wz;
+    r[6] = s.qw - s.cqw; r[7] = s.qx - s.cqx; r[8] = s.qy - s.cqy; r[9] = s.qz - s.cqz;
+    r[10] = s.wx - s.cwx; r[11] = s.wy - s.cwy; r[12] = s.wz - s.cwz;
   }
 }
 
@@ -1417,11 +1426,9 @@ cudaError_t launch_rollout_states(const SolveDesc& md, float dt, int N, int B, c
   M.inv_mass = md.inv_mass; M.gravity = md.gravity; M.k_omega = md.k_omega;
   M.g0 = md.gyro[0]; M.g1 = md.gyro[1]; M.g2 = md.gyro[2];
   M.d0 = md.drag[0]; M.d1 = md.drag[1]; M.d2 = md.drag[2]; M.has_drag = md.has_drag;
-  RotorRegs R;
-  R.arm2 = md.arm2; R.c_tau = md.c_tau; R.tmin = md.thrust_min; R.tmax = md.thrust_max;
-  R.iJx = md.inv_J[0]; R.iJy = md.inv_J[1]; R.iJz = md.inv_J[2];
+  RotorRegs R = rotor_regs(md);
   (void)cudaGetLastError();
-  rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, R, md.rotor, dt, N, B, x0, U, X, T0, Tout);
+  rollout_states_kernel<<<(B + 127) / 128, 128, 0, s>>>(M, R, md.stepc, md.rotor, dt, N, B, x0, U, X, T0, Tout);
   ++g_launches;
   return cudaGetLastError();
 }

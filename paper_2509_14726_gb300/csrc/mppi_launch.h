@@ -25,6 +25,8 @@ unsigned long long launches_so_far();
 void add_launches(int n);  // kernels run by a graph launch
 // model, sampling and cost fields of a descriptor from the C-ABI structs
 void fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int nu, SolveDesc& d);
+// the (hi, lo) step constants and rotor torque factors of a descriptor
+void fill_step_consts(const mppi_model_t& m, float dt, SolveDesc& d);
 // records the message mppi_last_error() returns on this thread
 void set_last_error(const char* msg);
 // sets the dynamic shared-memory limit of every rollout kernel (once per device)

@@ -18,3 +18,29 @@ def oracle_mod():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(autouse=True)
+def _clear_literal_misses():
+    try:
+        import parity_util
+    except ImportError:
+        yield
+        return
+    parity_util.LITERAL_MISSES.clear()
+    yield
+
+
+@pytest.hookimpl(hookwrapper=True)
+def pytest_runtest_makereport(item, call):
+    """A test whose only shortfall is a nominal-control miss beyond binary32
+    reach (parity_util.compare decides it from the oracle alone) is reported
+    as XFAIL with the literal errors, not as a pass."""
+    outcome = yield
+    rep = outcome.get_result()
+    if rep.when != "call" or not rep.passed:
+        return
+    pu = sys.modules.get("parity_util")
+    if pu is not None and pu.LITERAL_MISSES:
+        rep.outcome = "skipped"
+        rep.wasxfail = "nominal beyond binary32 reach: " + "; ".join(pu.LITERAL_MISSES)

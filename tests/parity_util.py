@@ -11,21 +11,26 @@ from typing import Optional
 
 import numpy as np
 
+from oracle.conditioning import binary32_floor
 from paper_2509_14726_gb300 import workloads as W
 
 # tolerances stated for this path: per-sample cost relative error, absolute
-# error of the nominal control (N or rad/s)
+# error of the nominal control (N or rad/s).  Both are asserted as stated.
 J_REL_TOL = 1e-4
 U_ABS_TOL = 1e-5
-# Binary32 rollouts carry a per-sample cost error; it reaches the nominal
-# through the weights (Eq. 4): dU_kj = (1/lambda) sum_m w_m (dJbar - dJ_m)
-# (u_mkj - U_kj), so |dU_kj| <= 2 DJ32 sens_kj with sens_kj the oracle's
-# (1/lambda) sum_m w_m |u_mkj - U_kj|.  DJ32 is the binary32 cost error of a
-# sample: trajectory error floor 2.5e-7 m rms / 6.5e-7 m max over 50 RK4
-# steps times the cost gradient (2 |p - target| q, about 10 for these
-# weights) -> 2.5e-6 .. 6.5e-6; measured on significantly weighted samples
-# up to 5e-6.  Where sens_kj < 1 this leaves U_ABS_TOL.
-DJ32 = 5e-6
+# A solve whose nominal the weights amplify beyond binary32 reach.  The
+# oracle alone decides it (oracle.conditioning.binary32_floor: the change of
+# its FP64 nominal when every cost moves by one binary32 unit roundoff of its
+# term magnitude).  A binary32 rollout carries several such roundoffs, so
+# where the floor exceeds U_ABS_TOL / 4 the literal bound is out of binary32
+# reach.  Such a case that misses U_ABS_TOL by no more than
+# FLOOR_FACTOR times its floor is reported as an expected failure (XFAIL, with
+# its literal error), never as a pass; any other miss fails.
+FLOOR_MIN = U_ABS_TOL / 4
+FLOOR_FACTOR = 4.0
+# literal misses of the running test that the floor explains (read by the
+# report hook in conftest.py, cleared before every test)
+LITERAL_MISSES: list = []
 
 
 @dataclasses.dataclass
@@ -67,23 +72,25 @@ def push_oracle_state(gpu, ora) -> None:
 
 
 def compare(gpu, r: dict, label: str = "", j_tol: float = J_REL_TOL, u_tol: float = U_ABS_TOL,
-            check_decisions: bool = True, measured_cost_bound: bool = False) -> dict:
+            check_decisions: bool = True) -> dict:
     """Element-wise comparison of one solve; returns the statistics and
-    asserts the tolerances (samples the oracle flags as within 1e-5 m of a
-    gate plane, opening edge or near-gate sphere are counted and excluded).
-
-    measured_cost_bound: the nominal tolerance takes the largest absolute
-    cost error of the weighted, unflagged samples in place of DJ32 when that
-    is larger (long horizons and large costs carry a larger absolute binary32
-    cost error; their relative error is still held to j_tol)."""
+    asserts the stated tolerances: per-sample cost relative error <= j_tol,
+    gate decisions identical, nominal control |dU| <= u_tol (1e-5 N or rad/s)
+    on every (step, input).  Samples the oracle flags as within 1e-5 m of a
+    gate plane, an opening edge or the near-gate sphere are counted and
+    excluded from the cost statistic.  A nominal miss passes only as an
+    expected failure, and only where the oracle's binary32 floor puts the
+    bound out of binary32 reach (see binary32_floor)."""
     K = gpu.K
     nu = 5 if gpu.sc.objective == 1 else 4
     J = gpu.costs()
     flag = r["near_flag"] != 0
     ok = ~flag
     denom = np.maximum(np.abs(r["J"]), r["Jabs"])
-    rel = np.abs(J - r["J"]) / np.where(denom > 0, denom, 1.0)
-    stats = {"K": K, "flagged": int(flag.sum()), "max_rel_J": float(rel[ok].max()) if ok.any() else 0.0}
+    dJ = np.abs(J - r["J"])
+    rel = dJ / np.where(denom > 0, denom, 1.0)
+    stats = {"K": K, "flagged": int(flag.sum()), "max_rel_J": float(rel[ok].max()) if ok.any() else 0.0,
+             "max_abs_J": float(dJ[ok].max()) if ok.any() else 0.0}
     npass, first = gpu.sample_info()
     if gpu.sc.objective == 0:
         mism = (npass != r["npass"]) | (first != r["first_pass"])
@@ -91,20 +98,19 @@ def compare(gpu, r: dict, label: str = "", j_tol: float = J_REL_TOL, u_tol: floa
         stats["decision_mismatch_flagged"] = int((mism & flag).sum())
     Unew = gpu.unew()
     dU = np.abs(Unew[:, :nu] - r["Unew"][:, :nu])
-    dj = DJ32
-    if measured_cost_bound:
-        wsig = ok & (r["w"] > 1e-8)
-        if wsig.any():
-            dj = max(DJ32, float(np.max(np.abs(J - r["J"])[wsig])))
-        stats["cost_error_bound"] = dj
-    tolU = np.maximum(u_tol, 2.0 * dj * r["sens"][:, :nu])
     stats["max_dU"] = float(dU.max())
     stats["max_du0"] = float(dU[0].max())
-    stats["max_dU_over_tol"] = float((dU / tolU).max())
-    stats["well_conditioned_share"] = float(np.mean(tolU == u_tol))
-    # the weight mass on samples whose decision differs (if any) explains a dU excess
+    stats["max_dU_over_tol"] = float(dU.max() / u_tol)
+    miss = stats["max_dU"] > u_tol
+    if miss:
+        floor = binary32_floor(r, gpu.sc.lam, nu)
+        stats["binary32_floor"] = floor
     assert stats["max_rel_J"] <= j_tol, f"{label} J rel err {stats}"
     if gpu.sc.objective == 0 and check_decisions:
         assert stats["decision_mismatch_unflagged"] == 0, f"{label} gate decisions differ {stats}"
-    assert stats["max_dU_over_tol"] <= 1.0, f"{label} nominal differs {stats}"
+    if miss:
+        floor = stats["binary32_floor"]
+        beyond = floor is not None and floor > FLOOR_MIN and stats["max_dU"] <= FLOOR_FACTOR * floor
+        assert beyond, f"{label} nominal differs {stats}"
+        LITERAL_MISSES.append(f"{label}: |dU| {stats['max_dU']:.3g} > {u_tol:g}, binary32 floor {floor:.3g}")
     return stats
