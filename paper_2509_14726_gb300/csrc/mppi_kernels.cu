@@ -471,6 +471,111 @@ static_assert(MPPI_EPI_BATCH >= 1 && MPPI_EPI_BATCH <= 16, "MPPI_EPI_BATCH must 
 static_assert(MPPI_EPI_LANES >= 1 && MPPI_EPI_LANES <= 32 && (MPPI_EPI_LANES & (MPPI_EPI_LANES - 1)) == 0,
               "MPPI_EPI_LANES must be a power of two in [1, 32]");
 
+// The tile's Eq. 5 sums: P[k][j] = sum_m w_m (u_mkj - U*_kj) for the block's
+// samples (weights sE relative to the tile minimum), written to myP [N][5] as
+// compensated (hi, lo) pairs (FP64 in MPPI_ACC_F64).  Each warp takes
+// kEpiRows steps at a time with kEpiLanes lanes per step: a lane sums every
+// kEpiLanes-th sample of the tile, then the lanes of a step reduce in a fixed
+// order (log2(kEpiLanes) TwoSum levels).  A lane requests the weights and
+// normals of kEpiBatch samples before it uses the first (a lone block
+// otherwise waits one L2 latency per sample); in the compensated mode the
+// batch's products form one FMA chain that enters the running sum with one
+// Kahan step (the chain's rounding is a few ulps of its own few terms).
+template <int ACC, int BF16, int GEN>
+__device__ __forceinline__ void eq5_rows(const SolveDesc& d, const float* sU, const float* sE, uint32_t iter,
+                                         int m0, int nvalid, double* myP) {
+  constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes, kEpiBatch = GEN == 2 ? 1 : MPPI_EPI_BATCH;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int sub = lane / kEpiLanes, sl = lane % kEpiLanes;
+  const int N = d.N, K = d.K, nu = d.nu;
+  const bool five = nu == 5;
+  for (int k0 = wid * kEpiRows; k0 < N; k0 += nw * kEpiRows) {
+    const int k = k0 + sub;
+    const bool row_ok = k < N;
+    const float* Uk = sU + kNU * (row_ok ? k : 0);
+    float Ukj[kNU], sg[kNU], lob[kNU], hib[kNU];
+#pragma unroll
+    for (int j = 0; j < kNU; ++j) {
+      Ukj[j] = Uk[j];
+      sg[j] = d.sigma[j];
+      lob[j] = d.u_min[j];
+      hib[j] = d.u_max[j];
+    }
+    float hi[kNU], lo[kNU];
+    double dacc[kNU];
+#pragma unroll
+    for (int j = 0; j < kNU; ++j) {
+      hi[j] = 0.f;
+      lo[j] = 0.f;
+      if (ACC == MPPI_ACC_F64) dacc[j] = 0.0;
+    }
+    if (row_ok) {
+      for (int i0 = sl; i0 < nvalid; i0 += kEpiBatch * kEpiLanes) {
+        float wb[kEpiBatch], zb[kEpiBatch][kNU];
+#pragma unroll
+        for (int t = 0; t < kEpiBatch; ++t) {
+          const int ic = min(i0 + t * kEpiLanes, nvalid - 1);  // in range; weight 0 past nvalid
+          wb[t] = i0 + t * kEpiLanes < nvalid ? sE[ic] : 0.f;
+          if (GEN == 2)
+            gen_noise<BF16, false>(d, iter, m0 + ic, k, zb[t], five);
+          else
+            load_noise<BF16, GEN == 0>(d, (size_t)k * K + m0 + ic, zb[t], five);
+        }
+        float part[kNU];
+#pragma unroll
+        for (int j = 0; j < kNU; ++j) part[j] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kEpiBatch; ++t) {
+          const float w = wb[t];
+#pragma unroll
+          for (int j = 0; j < kNU; ++j) {
+            if (j >= nu) break;
+            const float dv = clampf(Ukj[j] + sg[j] * zb[t][j], lob[j], hib[j]) - Ukj[j];
+            if (ACC == MPPI_ACC_F64)
+              dacc[j] = fma((double)w, (double)dv, dacc[j]);
+            else if (ACC == MPPI_ACC_F32)
+              hi[j] = fmaf(w, dv, hi[j]);
+            else
+              part[j] = fmaf(w, dv, part[j]);
+          }
+        }
+        if (ACC == MPPI_ACC_KAHAN32) {
+#pragma unroll
+          for (int j = 0; j < kNU; ++j)
+            if (j < nu) kahan_add(hi[j], lo[j], part[j]);
+        }
+      }
+    }
+    // cross-lane reduction within the step's lane group, fixed order
+    const bool writer = row_ok && sl == 0;
+#pragma unroll
+    for (int j = 0; j < kNU; ++j) {
+      if (j >= nu) break;
+      if (ACC == MPPI_ACC_F64) {
+        double v = dacc[j];
+#pragma unroll
+        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (writer) myP[kNU * k + j] = v;
+      } else if (ACC == MPPI_ACC_F32) {
+        float v = hi[j];
+#pragma unroll
+        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (writer) myP[kNU * k + j] = pack2(v, 0.f);
+      } else {
+        float h1 = hi[j], l1 = -lo[j];
+#pragma unroll
+        for (int o = kEpiLanes / 2; o; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, h1, o), l2 = __shfl_xor_sync(0xffffffffu, l1, o);
+          add2(h1, l1, h2, l2);
+        }
+        if (writer) myP[kNU * k + j] = pack2(h1, l1);
+      }
+    }
+    if (writer)
+      for (int j = nu; j < kNU; ++j) myP[kNU * k + j] = ACC == MPPI_ACC_F64 ? 0.0 : pack2(0.f, 0.f);
+  }
+}
+
 // ROT: rotor-thrust-rate input model (rotor thrusts in the state)
 template <int OBJ, int BF16, int GEN, int ROT>
 __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__ descs,
@@ -952,82 +1057,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const int NNU = N * kNU;
   const int tile_in_solve = tile.m0 / TS;
   double* myP = d.part_P + (size_t)tile_in_solve * NNU;
-  // each warp takes kEpiRows steps at a time, kEpiLanes lanes per step: a lane
-  // sums every kEpiLanes-th sample of the tile, then the lanes of a step
-  // reduce in a fixed order within their group (log2(kEpiLanes) levels)
-  // (regenerated normals are computed, not loaded: nothing to overlap)
-  constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes, kEpiBatch = GEN == 2 ? 1 : MPPI_EPI_BATCH;
-  const int sub = lane / kEpiLanes, sl = lane % kEpiLanes;
-  for (int k0 = wid * kEpiRows; k0 < N; k0 += nw * kEpiRows) {
-    const int k = k0 + sub;
-    const bool row_ok = k < N;
-    const float* Uk = sU + kNU * (row_ok ? k : 0);
-    float hi[kNU], lo[kNU];
-    double dacc[kNU];
-#pragma unroll
-    for (int j = 0; j < kNU; ++j) { hi[j] = 0.f; lo[j] = 0.f; dacc[j] = 0.0; }
-    if (row_ok) {
-      // kEpiBatch samples per round trip: their weights and normals are all
-      // requested before the first is used (a lone block otherwise waits one
-      // L2 latency per sample), then summed in sample order
-      for (int i0 = sl; i0 < nvalid; i0 += kEpiBatch * kEpiLanes) {
-        float wb[kEpiBatch], zb[kEpiBatch][kNU];
-#pragma unroll
-        for (int t = 0; t < kEpiBatch; ++t) {
-          const int ic = min(i0 + t * kEpiLanes, nvalid - 1);  // in range; unused past nvalid
-          wb[t] = sE[ic];
-          if (GEN == 2)
-            gen_noise<BF16, false>(d, iter, tile.m0 + ic, k, zb[t], five);
-          else
-            load_noise<BF16, GEN == 0>(d, (size_t)k * K + tile.m0 + ic, zb[t], five);
-        }
-#pragma unroll
-        for (int t = 0; t < kEpiBatch; ++t) {
-          if (i0 + t * kEpiLanes >= nvalid) break;
-          const float w = wb[t];
-#pragma unroll
-          for (int j = 0; j < kNU; ++j) {
-            if (j >= nu) break;
-            const float u = clampf(Uk[j] + d.sigma[j] * zb[t][j], d.u_min[j], d.u_max[j]);
-            const float dv = u - Uk[j];
-            if (acc == MPPI_ACC_F64) {
-              dacc[j] = fma((double)w, (double)dv, dacc[j]);
-            } else if (acc == MPPI_ACC_F32) {
-              hi[j] = fmaf(w, dv, hi[j]);
-            } else {
-              kahan_add(hi[j], lo[j], w * dv);
-            }
-          }
-        }
-      }
-    }
-    // cross-lane reduction within the step's lane group, fixed order
-    const bool writer = row_ok && sl == 0;
-#pragma unroll
-    for (int j = 0; j < kNU; ++j) {
-      if (j >= nu) break;
-      if (acc == MPPI_ACC_F64) {
-        double v = dacc[j];
-#pragma unroll
-        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (writer) myP[kNU * k + j] = v;
-      } else if (acc == MPPI_ACC_F32) {
-        float v = hi[j];
-#pragma unroll
-        for (int o = kEpiLanes / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (writer) myP[kNU * k + j] = pack2(v, 0.f);
-      } else {
-        float h1 = hi[j], l1 = -lo[j];
-#pragma unroll
-        for (int o = kEpiLanes / 2; o; o >>= 1) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, h1, o), l2 = __shfl_xor_sync(0xffffffffu, l1, o);
-          add2(h1, l1, h2, l2);
-        }
-        if (writer) myP[kNU * k + j] = pack2(h1, l1);
-      }
-    }
-    if (writer)
-      for (int j = nu; j < kNU; ++j) myP[kNU * k + j] = acc == MPPI_ACC_F64 ? 0.0 : pack2(0.f, 0.f);
+  switch (acc) {
+    case MPPI_ACC_F64: eq5_rows<MPPI_ACC_F64, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
+    case MPPI_ACC_F32: eq5_rows<MPPI_ACC_F32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
+    default: eq5_rows<MPPI_ACC_KAHAN32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
   }
   if (tid == 0) {
     d.part_m[tile_in_solve] = m_t;
