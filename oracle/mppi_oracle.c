@@ -147,8 +147,6 @@ typedef struct {
   double* theta0;     /* [2] theta and v_theta at the start of this solve */
   double* xref;       /* [N+1][13] tracking reference window */
   double* Xnom;       /* [N+1][13] rollout of the new nominal */
-  double* sens;       /* [N][5] (1/lambda) sum_m w_m |u_m - U*_new|: how much a
-                         cost perturbation moves each control (conditioning) */
   int32_t gate_at_start; /* gate index after the plant-crossing check */
   int32_t status;     /* 0 ok, 1 every cost non-finite (nominal kept) */
   double* Us;         /* [K][N][5] the clamped sampled sequences U^m (Eq. 3) */
@@ -704,16 +702,6 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
         if (j < nu)
           for (int32_t m = 0; m < K; ++m) s += w[m] * Us[((size_t)m * N + k) * OR_NU + j];
         Unew[OR_NU * k + j] = s;
-      }
-  }
-  if (out && out->sens) {
-    for (int32_t k = 0; k < N; ++k)
-      for (int j = 0; j < OR_NU; ++j) {
-        double s = 0.0;
-        if (j < nu && status == 0)
-          for (int32_t m = 0; m < K; ++m)
-            s += w[m] * fabs(Us[((size_t)m * N + k) * OR_NU + j] - Unew[OR_NU * k + j]);
-        out->sens[OR_NU * k + j] = s / pr->lambda;
       }
   }
   if (out && out->w) memcpy(out->w, w, sizeof(double) * K);

@@ -54,7 +54,7 @@ class OrState(C.Structure):
 class OrOut(C.Structure):
     _fields_ = [("Z_in", PD), ("Z", PD), ("J", PD), ("Jabs", PD), ("npass", PI), ("first_pass", PI),
                 ("near_flag", PI), ("w", PD), ("Unew", PD), ("u0", PD), ("passcnt", PI), ("theta0", PD),
-                ("xref", PD), ("Xnom", PD), ("sens", PD), ("gate_at_start", I32), ("status", I32), ("Us", PD)]
+                ("xref", PD), ("Xnom", PD), ("gate_at_start", I32), ("status", I32), ("Us", PD)]
 
 
 LIB_OMP_PATH = os.path.join(HERE, "liboracle_omp.so")
@@ -383,7 +383,6 @@ class OracleController:
             "first_pass": np.zeros(K, np.int32), "near_flag": np.zeros(K, np.int32), "w": np.zeros(K),
             "Unew": np.zeros((N, 5)), "u0": np.zeros(5), "passcnt": np.zeros(N + 1, np.int32),
             "theta0": np.zeros(2), "xref": np.zeros((N + 1, 13)), "Xnom": np.zeros((N + 1, 13)),
-            "sens": np.zeros((N, 5)),
         }
         if want_Z:
             res["Z"] = np.zeros((N, K, 5))
@@ -399,7 +398,6 @@ class OracleController:
         o.first_pass, o.near_flag, o.w = _pi(res["first_pass"]), _pi(res["near_flag"]), _pd(res["w"])
         o.Unew, o.u0, o.passcnt = _pd(res["Unew"]), _pd(res["u0"]), _pi(res["passcnt"])
         o.theta0, o.xref, o.Xnom = _pd(res["theta0"]), _pd(res["xref"]), _pd(res["Xnom"])
-        o.sens = _pd(res["sens"])
         rc = lib(self.omp).or_solve(C.byref(self.m), C.byref(self.p), C.byref(self.tv.c), C.byref(self.st), _pd(x0),
                             float(t0), C.byref(o))
         if rc < 0:

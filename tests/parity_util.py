@@ -78,7 +78,8 @@ def compare(gpu, r: dict, label: str = "", j_tol: float = J_REL_TOL, u_tol: floa
     gate decisions identical, nominal control |dU| <= u_tol (1e-5 N or rad/s)
     on every (step, input).  Samples the oracle flags as within 1e-5 m of a
     gate plane, an opening edge or the near-gate sphere are counted and
-    excluded from the cost statistic.  A nominal miss passes only as an
+    excluded from the cost statistic (at most 2 + K/1000 of them).  A nominal
+    miss passes only as an
     expected failure, and only where the oracle's binary32 floor puts the
     bound out of binary32 reach (see binary32_floor)."""
     K = gpu.K
@@ -105,6 +106,8 @@ def compare(gpu, r: dict, label: str = "", j_tol: float = J_REL_TOL, u_tol: floa
     if miss:
         floor = binary32_floor(r, gpu.sc.lam, nu)
         stats["binary32_floor"] = floor
+    # the near-boundary exclusion stays small: a few samples of thousands
+    assert stats["flagged"] <= 2 + K // 1000, f"{label} too many samples excluded {stats}"
     assert stats["max_rel_J"] <= j_tol, f"{label} J rel err {stats}"
     if gpu.sc.objective == 0 and check_decisions:
         assert stats["decision_mismatch_unflagged"] == 0, f"{label} gate decisions differ {stats}"

@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one slip in a copy of the oracle source (on the CPU),
-compiles it to a temporary library and runs the pin tests against it: at
-least one pin must fail.  This checks the pins, not the CUDA path.
+compiles it to a temporary library and runs the pin tests (including the
+whole-solve cross-check against tests/numpy_solve.py) against it: at least
+one pin must fail.  This checks the pins, not the CUDA path.
 """
 import os
 import subprocess
@@ -63,6 +64,20 @@ MUTATIONS = [
      "double hover = rotor ? 0.0 : md->mass * md->gravity;", "double hover = md->mass * md->gravity;"),
     ("rotor state not advanced by u0",
      "or_rotor_at(md, T0, Unew, pr->dt, st->rotor);", "or_rotor_at(md, T0, Unew, 0.0, st->rotor);"),
+    ("near-plane flag misses the end of the segment",
+     "if (fabs(info[0]) < eps || fabs(info[1]) < eps) flag |= 1;", "if (fabs(info[0]) < eps) flag |= 1;"),
+    ("near-edge flag on one side of the opening only",
+     "if (fabs(fabs(info[2]) - g[4]) < eps", "if (fabs(info[2] - g[4]) < eps"),
+    ("near-sphere flag never set",
+     "if (fabs(d0 - pr->r_near) < eps) flag |= 4;", "if (fabs(d0 - pr->r_near) < 0.0) flag |= 4;"),
+    ("gate cost scale drops the start distance",
+     "Jabs += fabs(dist2(xn, g)) + fabs(dist2(x, g)) + fabs(near);", "Jabs += fabs(dist2(xn, g)) + fabs(near);"),
+    ("contouring cost scale subtracts the progress reward",
+     "Jabs += lag + con + om + dv + dT + fabs(prog);", "Jabs += lag + con + om + dv + dT - prog;"),
+    ("path tangent not renormalised",
+     "for (int i = 0; i < 3; ++i) Tn[i] /= n;", "(void)n;"),
+    ("contouring state terms on the start state",
+     "double e[3] = {xn[0] - P[0], xn[1] - P[1], xn[2] - P[2]};", "double e[3] = {x[0] - P[0], x[1] - P[1], x[2] - P[2]};"),
     ("samples not clamped",
      "u[j] = clampd(Unom[OR_NU * k + j] + pr->sigma[j] * z[j], md->u_min[j], md->u_max[j]);",
      "u[j] = Unom[OR_NU * k + j] + pr->sigma[j] * z[j];"),

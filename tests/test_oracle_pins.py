@@ -842,3 +842,165 @@ def test_rotor_controller_state(oracle_mod):
     np.testing.assert_allclose(r["Unew"], np.einsum("m,mkj->kj", r["w"], us), atol=1e-12)
     np.testing.assert_allclose(ctl.rotor, np.clip(T0 + r["u0"][:4] * sc.dt, mc.thrust_min, mc.thrust_max),
                                atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# outputs that scale or filter the parity tests: near-boundary flags and the
+# cost-term magnitude J_abs (relative-error denominator)
+# ---------------------------------------------------------------------------
+
+def _line_solve(oracle_mod, x0, N, **kw):
+    """One solve of a single unperturbed sample (K = 1, caller normals all
+    zero) on the straight two-gate line: the hover input keeps the velocity,
+    so p_k = p_0 + k h v in closed form."""
+    tr = _line_track(2, spacing=6.0)
+    mc = _mc()
+    sc = W.SolveConfig(objective=kw.pop("objective", 0), K=1, N=N, dt=0.05, **kw)
+    ctl = oracle_mod.OracleController(mc, sc, tr)
+    return ctl.solve(np.asarray(x0, float), 0.0, Z_in=np.zeros((N, 1, 5))), tr, sc
+
+
+@pytest.mark.parametrize("ds,expect", [(3e-6, 1), (3e-4, 0)])
+def test_near_plane_flag(oracle_mod, ds, expect):
+    """A state within flag_eps (1e-5 m) of the gate plane sets bit 0; one
+    3e-4 m away sets nothing."""
+    vx, h = 5.0, 0.05
+    r, _, _ = _line_solve(oracle_mod, _state(p=(6.0 - 3 * vx * h + ds, 0.1, 2.05), v=(vx, 0, 0)), 8)
+    assert r["near_flag"][0] == expect
+    assert r["npass"][0] == 1
+
+
+@pytest.mark.parametrize("lat,expect_flag,expect_pass", [(0.75 - 3e-6, 2, 1), (0.75 + 3e-6, 2, 0),
+                                                         (-0.75 + 3e-6, 2, 1), (-0.75 - 3e-6, 2, 0),
+                                                         (0.75 - 3e-4, 0, 1), (0.75 + 3e-4, 0, 0)])
+def test_near_edge_flag(oracle_mod, lat, expect_flag, expect_pass):
+    """A crossing point within flag_eps of the opening's edge sets bit 1,
+    inside (counted pass) or outside (no pass); 3e-4 m from it, nothing."""
+    r, _, _ = _line_solve(oracle_mod, _state(p=(6.0 - 0.65, lat, 2.0), v=(5.0, 0, 0)), 8, q_near=0.0)
+    assert r["near_flag"][0] == expect_flag
+    assert r["npass"][0] == expect_pass
+
+
+@pytest.mark.parametrize("dr,expect", [(3e-6, 4), (-3e-6, 4), (3e-4, 0)])
+def test_near_sphere_flag(oracle_mod, dr, expect):
+    """A state p_k (k < N) within flag_eps of the near-gate sphere's radius
+    sets bit 2 (Eq. 7's conditional term switches there)."""
+    vx, h = 5.0, 0.05
+    r_near = 1.5
+    p0 = (6.0 - (r_near + dr) - 2 * vx * h, 0.0, 2.0)
+    r, _, _ = _line_solve(oracle_mod, _state(p=p0, v=(vx, 0, 0)), 6, r_near=r_near, q_near=0.5)
+    assert r["near_flag"][0] == expect
+
+
+def test_gate_cost_scale_closed_form(oracle_mod):
+    """J_abs of the gate objective is sum_k (||p_{k+1} - g||^2 + ||p_k - g||^2
+    + |near_k|) + penalties: on the straight line, without the near term and
+    before the gate, it follows from the closed-form positions."""
+    vx, h, N = 5.0, 0.05, 6
+    p0 = np.array([1.0, 0.3, 2.2])
+    r, tr, _ = _line_solve(oracle_mod, _state(p=p0, v=(vx, 0, 0)), N, q_near=0.0)
+    g = tr.gates[0, :3]
+    P = [p0 + np.array([vx * h * k, 0, 0]) for k in range(N + 1)]
+    expect = sum(np.sum((P[k + 1] - g) ** 2) + np.sum((P[k] - g) ** 2) for k in range(N))
+    assert abs(r["Jabs"][0] - expect) < 1e-9 * expect
+    # the cost itself telescopes
+    assert abs(r["J"][0] - (np.sum((P[N] - g) ** 2) - np.sum((P[0] - g) ** 2))) < 1e-9
+
+
+def test_tracking_cost_scale_equals_cost(oracle_mod):
+    """Every Eq. 8 term is non-negative, so J_abs = J for tracking."""
+    tr = W.random_course(7)
+    mc = _mc()
+    sc = W.SolveConfig(objective=2, K=16, N=10, dt=0.02)
+    x0 = oracle_mod.ref_eval(tr, 0.2)
+    x0[0:3] += 0.3
+    r = oracle_mod.OracleController(mc, sc, tr).solve(x0, 0.2)
+    assert np.all(r["J"] > 0)
+    np.testing.assert_allclose(r["Jabs"], r["J"], rtol=1e-14)
+
+
+def test_contouring_cost_scale_counts_the_progress_reward_positive(oracle_mod):
+    """Eq. 9's only negative term is the progress reward -mu v_theta, so
+    J_abs - J = 2 mu sum_k v_{k+1}; with a constant progress acceleration a
+    from rest, v_{k+1} = (k + 1) a h."""
+    N, h = 8, 0.05
+    tr = _line_track(2)
+    mc = _mc()
+    sc = W.SolveConfig(objective=1, K=1, N=N, dt=h, mu=0.7)
+    z5 = 0.2
+    Z = np.zeros((N, 1, 5))
+    Z[:, 0, 4] = z5
+    a = sc.sigma[4] * z5
+    r = oracle_mod.OracleController(mc, sc, tr).solve(_state(p=(0.0, 0.2, 2.0)), 0.0, Z_in=Z)
+    expect = 2 * sc.mu * sum((k + 1) * a * h for k in range(N))
+    assert abs((r["Jabs"][0] - r["J"][0]) - expect) < 1e-12
+
+
+def test_binary32_floor_closed_form():
+    """The conditioning floor of two samples: with the costs (0, D) and only
+    the second one perturbed (J_abs = (0, A)), the floor is the larger change
+    of U = (u1 + e u2) / (1 + e), e = exp(-D / lambda), over the signs drawn."""
+    from oracle.conditioning import U32, binary32_floor
+    lam, D, A = 0.7, 0.3, 250.0
+    u1, u2 = np.array([[1.0, -2.0]]), np.array([[4.0, 1.0]])
+    Us = np.stack([u1, u2])
+    J = np.array([0.0, D])
+
+    def U(d):
+        e = math.exp(-d / lam)
+        return (u1 + e * u2) / (1 + e)
+    r = {"J": J, "Jabs": np.array([0.0, A]), "Us": Us, "Unew": U(D)}
+    rng = np.random.default_rng(12345)
+    signs = {int(rng.choice([-1.0, 1.0], size=2)[1]) for _ in range(8)}
+    expect = max(np.max(np.abs(U(D + s * U32 * A) - U(D))) for s in signs)
+    assert abs(binary32_floor(r, lam, 2) - expect) < 1e-15
+    # first order: |u2 - u1| w1 w2 u A / lambda
+    w2 = math.exp(-D / lam) / (1 + math.exp(-D / lam))
+    assert abs(expect - np.max(np.abs(u2 - u1)) * (1 - w2) * w2 * U32 * A / lam) < 1e-3 * expect
+
+
+# ---------------------------------------------------------------------------
+# whole solves: the C oracle against an independent NumPy statement
+# ---------------------------------------------------------------------------
+
+def _cross_cases():
+    mc, sc, tr, x0 = W.c1_single_gate()
+    sc.K, sc.N = 48, 8
+    x0 = np.array(x0, float)
+    g = tr.gates[0]
+    x0[3:6] = 4.0 * np.array([math.cos(g[3]), math.sin(g[3]), 0.0])  # flies through gate 0
+    yield "gate", mc, sc, tr, x0, [0.05 * i for i in range(7)]
+    for obj, name in ((1, "contour"), (2, "track")):
+        mc, sc, tr, x0 = W.c2_full_scale(obj, 7)
+        sc.K, sc.N = 48, 8
+        yield name, mc, sc, tr, np.array(x0, float), [0.3, 0.32, 0.34]
+
+
+@pytest.mark.parametrize("name", ["gate", "contour", "track"])
+def test_c_oracle_equals_numpy_solve(oracle_mod, name):
+    """Consecutive solves (K = 48, N = 8, the plant stepping with u0 between
+    them: warm start, temporal rule, gate advance, progress state) agree with
+    tests/numpy_solve.py: costs and their term magnitudes to 1e-12 relative,
+    the new nominal to 1e-12, gate decisions exactly."""
+    import numpy_solve as NS
+    case = [c for c in _cross_cases() if c[0] == name][0]
+    _, mc, sc, tr, x, t0s = case
+    if name == "track":
+        x = oracle_mod.ref_eval(tr, t0s[0])
+        x[0:3] += 0.1
+    a, b = oracle_mod.OracleController(mc, sc, tr), NS.NumpyController(mc, sc, tr)
+    passes = 0
+    for t0 in t0s:
+        ra, rb = a.solve(x, t0), b.solve(x, t0)
+        ok = ra["near_flag"] == 0
+        assert ok.sum() >= sc.K - 2
+        den = np.maximum(np.abs(ra["J"]), ra["Jabs"])
+        assert np.max(np.abs(ra["J"] - rb["J"])[ok] / den[ok]) < 1e-12
+        np.testing.assert_allclose(rb["Jabs"][ok], ra["Jabs"][ok], rtol=1e-12)
+        np.testing.assert_allclose(rb["Unew"], ra["Unew"], rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(rb["npass"][ok], ra["npass"][ok])
+        np.testing.assert_array_equal(rb["first_pass"][ok], ra["first_pass"][ok])
+        passes += int(ra["npass"].max())
+        x = oracle_mod.rk4_step(mc, x, ra["u0"][:4], sc.dt)
+    if name == "gate":
+        assert passes > 0 and a.gate == b.gate == 1  # samples pass, and so does the plant
