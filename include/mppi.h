@@ -267,6 +267,21 @@ int mppi_import_state(mppi_handle h, const void* buf, size_t size);
  * collective-thrust handle. */
 int mppi_set_rotor_thrusts(mppi_handle h, const float T[4]);
 int mppi_get_rotor_thrusts(mppi_handle h, float T[4]);
+/* The rollout kernel waits for the bulk copies that stage the nominal and
+ * the path table in shared memory with a bounded wait; a wait that gives up
+ * marks its block's samples invalid and the solve returns MPPI_ERR_TIMEOUT
+ * (mppi_solve, mppi_batch_solve; the device status of the asynchronous
+ * calls), keeping the nominal when no sample is left.  limit_ns sets that
+ * wait's bound (default 2e8 ns).  unreachable = 1 is a testing switch: the
+ * wait then targets a barrier that nothing completes, so it runs out; the
+ * copies themselves still complete before the block goes on.  Not in the
+ * paper: failure reporting of this implementation. */
+int mppi_set_copy_wait(mppi_handle h, uint32_t limit_ns, int32_t unreachable);
+
+/* Sets the absolute index of the gate the next solve targets (Sec. IV-A: the
+ * gate the drone flies toward; indices keep counting past the last gate of a
+ * closed track).  MPPI_ERR_ARG for a negative index; mppi_import_state
+ * refuses a blob with one too. */
 int mppi_set_gate_index(mppi_handle h, int32_t gate);
 
 /* Uses caller-provided standard normals for the next solve instead of
@@ -333,9 +348,9 @@ int mppi_rollout_states_rotor(const mppi_model_t* model, float dt, int32_t N, in
  * clears what must start at zero.  Calls whose work overlaps on the GPU (two
  * streams, or two threads) race on the array and give wrong results: issue
  * them on one stream, or order them.  Asynchronous: returns after enqueueing
- * on `stream`.  Errors: MPPI_ERR_ARG (null pointer, bad sizes, scratch limit, a
- * rotor-thrust-rate model: its rotor thrusts are handle state),
- * MPPI_ERR_CUDA. */
+ * on `stream`.  Errors: MPPI_ERR_ARG (null pointer, bad sizes, scratch limit,
+ * a negative gate index, a rotor-thrust-rate model: its rotor thrusts are
+ * handle state), MPPI_ERR_CUDA. */
 int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t* params, const mppi_track_t* d_track,
                        const float* d_x0, double t0, const float* d_U, uint32_t iter, int32_t gate,
                        void* stream, float* d_Unew, float* d_u0);
@@ -384,13 +399,21 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
                           const mppi_track_t* track, int32_t* drone_out);
 /* Queues n requests (host arrays: drones [n], x0s [n][13], t0s [n], Ks [n],
  * Ns [n]); writes their ids (may be NULL).  A request whose K or N exceeds
- * its drone's caps, or whose scratch exceeds the whole pool, is refused with
- * MPPI_ERR_NOT_ADMITTED (none of the n is queued then). */
+ * its drone's caps, whose scratch exceeds the whole pool, or whose tiles
+ * exceed what one batch holds, is refused with MPPI_ERR_NOT_ADMITTED (none of
+ * the n is queued then). */
 int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const float* x0s, const double* t0s,
                        const int32_t* Ks, const int32_t* Ns, int64_t* ids_out);
 /* Admits and launches at most one batch if a slot is free; writes how many
- * requests it launched (0 if none could be admitted). */
+ * requests it launched (0 if none could be admitted).  If the transfer or a
+ * launch of the batch fails, the admitted requests are handed back (scratch
+ * released, drones idle, requests queued again in arrival order) and the call
+ * returns MPPI_ERR_CUDA; a later step retries them. */
 int mppi_server_step(mppi_server s, int32_t* launched);
+/* Testing hook for that recovery path (no counterpart in the paper): the
+ * next mppi_server_step that admits a batch fails on the host, before any
+ * transfer or launch, as if the batch's first launch had failed. */
+int mppi_server_fail_next_launch(mppi_server s);
 /* Collects finished requests (up to cap) into out; writes their count. */
 int mppi_server_poll(mppi_server s, mppi_result_t* out, int32_t cap, int32_t* n_out);
 /* [0] queued, [1] in flight, [2] scratch bytes in use, [3] peak scratch

@@ -300,6 +300,8 @@ void mppi::fill_step_consts(const mppi_model_t& m, float dt, SolveDesc& d) {
 
 void mppi::fill_model_params(const mppi_model_t& m, const mppi_params_t& p, int nu, SolveDesc& d) {
   fill_step_consts(m, p.dt, d);
+  d.wait_ns = 200000000u;  // 0.2 s for a few KB of bulk copies
+  d.wait_unreachable = 0;
   d.mass = m.mass;
   d.inv_mass = (float)(1.0 / (double)m.mass);
   d.gravity = m.gravity;
@@ -671,7 +673,17 @@ int mppi_solve(mppi_handle h, const float x0[13], double t0, void* stream, float
   CU(cudaEventSynchronize(h->ev_u0));
   for (int i = 0; i < kNU; ++i) u0_out[i] = ((volatile float*)h->io.u0)[i];
   const int st = ((volatile int32_t*)h->io.status)[0];
+  if (st == MPPI_ERR_TIMEOUT) return fail(MPPI_ERR_TIMEOUT, "a bounded wait for the bulk copies gave up");
   if (st == MPPI_WARN_DEGENERATE) return fail(MPPI_WARN_DEGENERATE, "every sample cost was non-finite");
+  return MPPI_OK;
+}
+
+int mppi_set_copy_wait(mppi_handle h, uint32_t limit_ns, int32_t unreachable) {
+  if (!h) return fail(MPPI_ERR_ARG, "null handle");
+  h->hd.wait_ns = limit_ns;
+  h->hd.wait_unreachable = unreachable ? 1 : 0;
+  CU(cudaMemcpy(h->d_desc, &h->hd, sizeof h->hd, cudaMemcpyHostToDevice));
+  ++h->version;
   return MPPI_OK;
 }
 
@@ -814,6 +826,9 @@ int mppi_import_state(mppi_handle h, const void* buf, size_t size) {
   if (hd.magic != kMagic || hd.version != 1u || (int)hd.N_cap != h->N_cap || (int)hd.nu != h->nu)
     return fail(MPPI_ERR_ARG, "state blob does not match this handle");
   c += sizeof hd;
+  DevState st;
+  memcpy(&st, c, sizeof st);
+  if (st.gate < 0) return fail(MPPI_ERR_ARG, "state blob has a negative gate index");
   CU(cudaMemcpy(h->hd.st, c, sizeof(DevState), cudaMemcpyHostToDevice));
   c += sizeof(DevState);
   CU(cudaMemcpy(h->hd.U, c, sizeof(float) * h->N_cap * kNU, cudaMemcpyHostToDevice));
@@ -824,6 +839,7 @@ int mppi_import_state(mppi_handle h, const void* buf, size_t size) {
 
 int mppi_set_gate_index(mppi_handle h, int32_t gate) {
   if (!h) return fail(MPPI_ERR_ARG, "null handle");
+  if (gate < 0) return fail(MPPI_ERR_ARG, "gate index %d is negative", (int)gate);
   CU(cudaMemcpy(&h->hd.st->gate, &gate, sizeof gate, cudaMemcpyHostToDevice));
   return MPPI_OK;
 }
@@ -1208,6 +1224,9 @@ int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* st
   }
   CU(cudaEventSynchronize(b->ev));
   memcpy(u0s_out, (const void*)b->io.u0, sizeof(float) * 5 * b->n);
+  for (int i = 0; i < b->n; ++i)
+    if (((volatile int32_t*)b->io.status)[i] == MPPI_ERR_TIMEOUT)
+      return fail(MPPI_ERR_TIMEOUT, "solve %d: a bounded wait for the bulk copies gave up", i);
   for (int i = 0; i < b->n; ++i)
     if (((volatile int32_t*)b->io.status)[i] == MPPI_WARN_DEGENERATE)
       return fail(MPPI_WARN_DEGENERATE, "solve %d: every sample cost was non-finite", i);

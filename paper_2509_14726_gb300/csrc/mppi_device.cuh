@@ -42,7 +42,7 @@ struct DevState {
   float rotor[4];      // rotor model: rotor thrusts at the next x0 (integrated commands)
   float rotor_prev[4]; // rotor thrusts at the x0 of the last solve (its nominal rollout)
   int32_t has_rotor;   // 0: hover thrust
-  int32_t pad_;
+  int32_t timeouts_seen;  // value of timeouts when the last solve ended
 };
 
 // Step constants as (hi, lo) binary32 pairs, so that the RK4 weights h/6,
@@ -117,6 +117,8 @@ struct SolveDesc {
   float arm2, c_tau, thrust_min, thrust_max, inv_J[3];
   float kt[3][2];       // torque factors l/sqrt2/Jx, l/sqrt2/Jy, c_tau/Jz as (hi, lo)
   int32_t spt;          // samples per thread: a tile holds block x spt samples
+  uint32_t wait_ns;     // limit of the rollout's first wait for its bulk copies
+  int32_t wait_unreachable;  // testing: that wait targets a barrier nothing completes
 };
 
 // samples one rollout block covers

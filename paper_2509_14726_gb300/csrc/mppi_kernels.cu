@@ -186,12 +186,15 @@ __device__ __forceinline__ GateF load_gate(const GateF* table, int i) {
   return g;
 }
 
+// table row of absolute gate index idx: modulo n on a closed track; on an
+// open track the last gate stays targeted (and a negative index, which the
+// host API refuses, reads row 0 rather than outside the table)
 __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
   if (closed) {
     int r = idx % n;
     return r < 0 ? r + n : r;
   }
-  return idx < n ? idx : n - 1;
+  return idx < 0 ? 0 : (idx < n ? idx : n - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -582,7 +585,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
                                                             const Tile* __restrict__ tiles, LaunchIO io) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) SolveDesc sd;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar, mbar_never;
   __shared__ double red[32];
   __shared__ float x0s[kNX];
   __shared__ float4 sBnd[5];  // (sigma, u_min, u_max, 0) per input; (w_limit, omega_max, z_floor, 0)
@@ -629,6 +632,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const uint32_t bytes_path = (OBJ == MPPI_OBJ_CONTOUR && path_smem) ? align16((uint32_t)d.S * 24u) : 0u;
   if (tid == 0) {
     mbar_init(&mbar, 1);
+    if (d.wait_unreachable) mbar_init(&mbar_never, 1);
     s_bad = 0;
   }
   __syncthreads();
@@ -717,7 +721,12 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     }
   }
   // ---- wait for the bulk copies (bounded) ----
-  if (!mbar_wait(&mbar, 0, 200000000ull)) {
+  // A wait that gives up marks the block's samples invalid and counts a
+  // timeout, which the solve reports as MPPI_ERR_TIMEOUT; a second bounded
+  // wait then lets the copies land before the block uses or releases the
+  // shared memory they write.  (For testing, the first wait can target a
+  // barrier that no copy ever completes.)
+  if (!mbar_wait(d.wait_unreachable ? &mbar_never : &mbar, 0, d.wait_ns)) {
     if (tid == 0) { s_bad = 1; atomicAdd(&st->timeouts, 1); }
     mbar_wait(&mbar, 0, 200000000ull);
   }
@@ -1156,7 +1165,11 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       st->gate0 = st->gate + (OBJ == MPPI_OBJ_GATE ? s_adv : 0);
       st->adv = OBJ == MPPI_OBJ_GATE ? s_adv : 0;
       st->gate = st->gate0;
-      st->status = degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
+      // timeouts counted by any block of this solve (before its ticket)
+      const int32_t to = atomicAdd(&st->timeouts, 0);
+      const int status = to != st->timeouts_seen ? MPPI_ERR_TIMEOUT : degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
+      st->timeouts_seen = to;
+      st->status = status;
       st->iter += 1u;
       st->has_prev = 1;
       st->n_nom = N;
@@ -1182,7 +1195,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       }
       st->scal[2] = s_m;
       st->scal[3] = S_total;
-      if (io.status) io.status[tile.solve] = degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
+      if (io.status) io.status[tile.solve] = status;
       d.ticket[0] = 0u;
     }
   }

@@ -141,6 +141,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
     return fail(MPPI_ERR_ARG, "samples_per_thread out of range");
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
+  if (gate < 0) return fail(MPPI_ERR_ARG, "gate index is negative");
   if (p.objective == MPPI_OBJ_GATE && (d_track->n_gates < 1 || !d_track->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs gates");
   if (p.objective == MPPI_OBJ_CONTOUR && (d_track->S < 2 || !d_track->path || !(d_track->L > 0)))

@@ -171,6 +171,7 @@ struct Slot {
 struct mppi_server_s {
   int device = 0;
   int max_drones = 0, max_batch = 0, max_tiles = 0;
+  bool fail_next_launch = false;  // testing hook: the next admitted batch fails on the host
   std::vector<Drone> drones;
   char* pool_base = nullptr;
   Pool pool;
@@ -407,6 +408,9 @@ int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const fl
     const Scratch sc = scratch_for(Ks[i], Ns[i], d.block, d.nu == 5, d.hd.noise_bf16, d.hd.noise_gen);
     if (sc.total > s->pool.size())
       return sfail(MPPI_ERR_NOT_ADMITTED, "request needs %zu scratch bytes, the pool has %zu", sc.total, s->pool.size());
+    const int T = (Ks[i] + d.block * d.hd.spt - 1) / (d.block * d.hd.spt);
+    if (T > s->max_tiles)
+      return sfail(MPPI_ERR_NOT_ADMITTED, "request needs %d tiles, a batch holds %d", T, s->max_tiles);
   }
   const double t = now_s();
   for (int i = 0; i < n; ++i) {
@@ -557,8 +561,30 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   }
   int32_t* hwhich = reinterpret_cast<int32_t*>(sl.host + st.which);
   if (!which.empty()) memcpy(hwhich, which.data(), sizeof(int32_t) * which.size());
+  // a failure from here on hands the admitted requests back: their scratch
+  // returns to the pool, their drones become idle, and they rejoin the queue
+  // in arrival order (request ids grow with arrival)
+  auto undo = [&](cudaError_t e, const char* what) {
+    for (Request& r : batch) {
+      s->pool.release(r.off, r.bytes);
+      s->drones[r.drone].busy = false;
+      r.t_launch = 0.0;
+      s->queue.push_back(r);
+    }
+    std::sort(s->queue.begin(), s->queue.end(), [](const Request& a, const Request& b) { return a.id < b.id; });
+    return sfail(MPPI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+#define SCU_UNDO(call)                  \
+  do {                                  \
+    cudaError_t e_ = (call);            \
+    if (e_ != cudaSuccess) return undo(e_, #call); \
+  } while (0)
+  if (s->fail_next_launch) {
+    s->fail_next_launch = false;
+    return undo(cudaErrorLaunchFailure, "injected failure (mppi_server_fail_next_launch)");
+  }
   cudaStream_t stm = sl.stream;
-  SCU(cudaMemcpyAsync(sl.dev, sl.host, st.total, cudaMemcpyHostToDevice, stm));
+  SCU_UNDO(cudaMemcpyAsync(sl.dev, sl.host, st.total, cudaMemcpyHostToDevice, stm));
   const SolveDesc* ddesc = reinterpret_cast<const SolveDesc*>(sl.dev + st.descs);
   const Tile* dtiles = reinterpret_cast<const Tile*>(sl.dev + st.tiles);
   LaunchIO io;
@@ -569,18 +595,26 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   io.status = sl.d_status;
   for (size_t q = 0; q < groups.size(); ++q)
     if (groups[q].gen == MPPI_NOISEGEN_KERNEL)
-      SCU(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm,
-                       groups[q].nom));
+      SCU_UNDO(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm,
+                            groups[q].nom));
   for (size_t q = 0; q < groups.size(); ++q)
-    SCU(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
-                       groups[q].block, groups[q].smem, io, stm, groups[q].gen, groups[q].rot));
-  SCU(launch_nominal(ddesc, reinterpret_cast<const int32_t*>(sl.dev + st.which), (int)which.size(), stm));
-  SCU(cudaEventRecord(sl.done, stm));
+    SCU_UNDO(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
+                            groups[q].block, groups[q].smem, io, stm, groups[q].gen, groups[q].rot));
+  SCU_UNDO(launch_nominal(ddesc, reinterpret_cast<const int32_t*>(sl.dev + st.which), (int)which.size(), stm));
+  SCU_UNDO(cudaEventRecord(sl.done, stm));
+#undef SCU_UNDO
   sl.reqs.swap(batch);
   sl.busy = true;
   s->next_slot = (si + 1) % (int)s->slots.size();
   s->batches += 1;
   if (launched) *launched = (int32_t)sl.reqs.size();
+  return MPPI_OK;
+}
+
+int mppi_server_fail_next_launch(mppi_server s) {
+  if (!s) return sfail(MPPI_ERR_ARG, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->fail_next_launch = true;
   return MPPI_OK;
 }
 

@@ -114,6 +114,8 @@ def load():
         "mppi_server_stats": ([vp, C.POINTER(C.c_double)], C.c_int),
         "mppi_server_export_drone": ([vp, I32, vp, C.POINTER(sz)], C.c_int),
         "mppi_server_destroy": ([vp], C.c_int),
+        "mppi_server_fail_next_launch": ([vp], C.c_int),
+        "mppi_set_copy_wait": ([vp, C.c_uint32, I32], C.c_int),
         "mppi_solve_noalloc": ([C.POINTER(Model), C.POINTER(Params), C.POINTER(TrackC), vp, C.c_double, vp, U32, I32,
                                 vp, vp, vp], C.c_int),
         "mppi_last_error": ([], C.c_char_p),
@@ -452,6 +454,11 @@ class Controller:
         mppi_set_shape(self.h, K, N)
         self.K, self.N = K, N
 
+    def set_copy_wait(self, limit_ns: int, unreachable: bool = False) -> None:
+        """Bound of the rollout's wait for its bulk copies; unreachable makes
+        that wait target a barrier nothing completes (testing the timeout)."""
+        _check(load().mppi_set_copy_wait(C.c_void_p(self.h), int(limit_ns), int(bool(unreachable))))
+
     def rotor_thrusts(self) -> np.ndarray:
         """Rotor model: the rotor thrusts the next solve starts from."""
         return mppi_get_rotor_thrusts(self.h)
@@ -493,7 +500,8 @@ class Controller:
         mppi_import_state(self.h, blob)
 
 
-# DevState: 10 int32, theta, v_theta, c_last + prev_x0[13], scal[4], rotor[4], rotor_prev[4], has_rotor, pad
+# DevState: 10 int32, theta, v_theta, c_last + prev_x0[13], scal[4], rotor[4], rotor_prev[4], has_rotor,
+# timeouts_seen
 _DEVSTATE_FMT = "<10i2d14f4d8f2i"
 
 
@@ -600,6 +608,10 @@ class Server:
         n = I32()
         _check(load().mppi_server_poll(C.c_void_p(self.h), out.ctypes.data, int(cap), C.byref(n)))
         return out[: n.value]
+
+    def fail_next_launch(self) -> None:
+        """Testing hook: the next step that admits a batch fails on the host."""
+        _check(load().mppi_server_fail_next_launch(C.c_void_p(self.h)))
 
     def stats(self) -> dict:
         a = (C.c_double * 8)()

@@ -531,3 +531,31 @@ def test_solve_batch_cache_under_threads(M):
     for t in threads:
         t.join()
     assert not errors, errors[:3]
+
+
+def test_bounded_wait_reports_a_timeout_and_keeps_the_nominal(O, M):
+    """The rollout's wait for its bulk copies is bounded.  Pointed at a barrier
+    that nothing completes (a 1 ms limit), it gives up: the solve returns
+    MPPI_ERR_TIMEOUT, no sample is used and the nominal is kept (U*_new = U*,
+    u0 = U*[0]), the context stays usable, and with the normal wait the next
+    solve matches the oracle."""
+    case = c1_case()
+    gpu, ora = make_pair(case)
+    U_before = gpu.nominal().copy()
+    gpu.set_copy_wait(1_000_000, unreachable=True)
+    with pytest.raises(M.MppiError) as e:
+        gpu.solve(case.x0, 0.0)
+    assert e.value.code == M.MPPI_ERR_TIMEOUT
+    np.testing.assert_array_equal(gpu.unew(), U_before)
+    assert M.decode_state(gpu.export_state(), case.sc.N)["status"] == M.MPPI_ERR_TIMEOUT
+    # the same handle, normal wait: the oracle's solve from the state the failed
+    # solve left (its iteration counter advanced, the nominal shifted)
+    gpu.set_copy_wait(200_000_000, unreachable=False)
+    after = M.decode_state(gpu.export_state(), case.sc.N)
+    assert after["iter"] == 1
+    ora.set_state(U=after["U"][: case.sc.N], iter=after["iter"])
+    x = case.x0
+    gpu.solve(x, 0.0)
+    r = ora.solve(x, 0.0)
+    compare(gpu, r, "after a timed-out solve")
+    gpu.close()

@@ -110,3 +110,35 @@ def test_serving_loop_runs_a_fleet(M):
     out = serving.run_served(fleet, sched, budget_bytes=2 << 30, n_slots=3, max_batch=256, K_cap=4096, N_cap=50)
     assert out["finished"] == out["offered"]
     assert out["p99_ms"] < 1000.0
+
+
+def test_failed_launch_hands_the_batch_back(M):
+    """A batch whose launch fails (injected on the host, before any transfer
+    or launch) returns its requests to the queue: the step reports
+    MPPI_ERR_CUDA, no scratch stays in use, no drone stays busy, and the next
+    steps serve every request with the result it gets alone."""
+    fleet = _fleet(4)
+    srv = M.Server(len(fleet), 1 << 30, n_slots=2, max_batch=8)
+    alone = []
+    for d in fleet:
+        sc = W.SolveConfig(objective=d.objective, K=1024, N=20, dt=0.02, drone_id=d.drone_id)
+        srv.add_drone(W.ModelConfig(), sc, d.track, 2048, 30)
+        alone.append(M.Controller(W.ModelConfig(), sc, d.track, K_cap=2048, N_cap=30))
+    X0 = np.array([d.x0 for d in fleet])
+    n = len(fleet)
+    ids = srv.submit(np.arange(n), X0, np.zeros(n), np.full(n, 1024), np.full(n, 20))
+    srv.fail_next_launch()
+    with pytest.raises(M.MppiError) as e:
+        srv.step()
+    assert e.value.code == M.MPPI_ERR_CUDA
+    st = srv.stats()
+    assert st["queued"] == n and st["in_flight"] == 0 and st["scratch_used"] == 0
+    res = _drain(srv, n)
+    assert len(res) == n
+    by_id = {int(r[0]): r for r in res}
+    for i, c in enumerate(alone):
+        u, _ = c.solve(X0[i], 0.0)
+        np.testing.assert_array_equal(np.asarray(by_id[int(ids[i])][5], np.float32), u)
+        c.close()
+    srv.close()
+

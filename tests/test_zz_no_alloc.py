@@ -46,27 +46,41 @@ def _device_track(M, tr):
     return t, (gates, path, ref)
 
 
-def test_noalloc_matches_the_handle_path_twice(M):
-    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_GATE)
+@pytest.mark.parametrize("noise", ["f32", "bf16"])
+@pytest.mark.parametrize("objective", [W.OBJ_GATE, W.OBJ_CONTOUR, W.OBJ_TRACK])
+def test_noalloc_matches_the_handle_path_twice(M, objective, noise):
+    """Two calls in a row (the second warm-started from the first's result)
+    against a handle put in the same state before each of its solves: the
+    nominal, the Philox iteration and no other history (the allocation-free
+    call is stateless).  Each objective, with float32 and bfloat16 noise
+    storage, on one stream."""
+    mc, sc, tr, x0 = W.c2_full_scale(objective)
+    sc.K, sc.N = 2048, 40
     sc.temporal_rule = 0  # stateless call: no pass counts of a previous nominal
     mc, sc, tr = W.f32_model(mc), W.f32_solve(sc), tr.as_f32()
-    ctl = M.Controller(mc, sc, tr)
+    t0 = 0.3
+    if objective == W.OBJ_TRACK:
+        x0 = tr.ref[int(round(t0 / tr.dt_ref)) % tr.ref.shape[0]].copy()
+    nu = 5 if objective == W.OBJ_CONTOUR else 4
+    ctl = M.Controller(mc, sc, tr, noise_dtype=M.NOISE_BF16 if noise == "bf16" else M.NOISE_F32)
     d_track, keep = _device_track(M, tr)
     stream = torch.cuda.Stream()
     d_x0 = torch.tensor(np.float32(x0), device="cuda")
     d_u0_h = torch.zeros(5, dtype=torch.float32, device="cuda")
     d_u0_s = torch.zeros(5, dtype=torch.float32, device="cuda")
-    d_U = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
-    d_U[:, 0] = float(np.float32(mc.mass) * np.float32(mc.gravity))
+    U = np.zeros((sc.N, 5), np.float32)
+    U[:, 0] = np.float32(mc.mass) * np.float32(mc.gravity)
     d_Unew = torch.zeros((sc.N, 5), dtype=torch.float32, device="cuda")
     free_before_second = None
     for call in range(2):
+        d_U = torch.tensor(U, device="cuda")
+        ctl.import_state(M.encode_state(sc.N, nu, U, iter=call, n_nom=sc.N if call else 0))
         with torch.cuda.stream(stream):
-            M.mppi_solve_async(ctl.h, d_x0.data_ptr(), 0.0, stream, d_u0_h.data_ptr())
+            M.mppi_solve_async(ctl.h, d_x0.data_ptr(), t0, stream, d_u0_h.data_ptr())
             if call == 1:
                 torch.cuda.synchronize()
                 free_before_second = torch.cuda.mem_get_info()[0]
-            M.mppi_solve_noalloc(ctl.model, ctl.params, d_track, d_x0.data_ptr(), 0.0, d_U.data_ptr(), call, 0,
+            M.mppi_solve_noalloc(ctl.model, ctl.params, d_track, d_x0.data_ptr(), t0, d_U.data_ptr(), call, 0,
                                  stream, d_Unew.data_ptr(), d_u0_s.data_ptr())
         stream.synchronize()
         if call == 1:
@@ -75,10 +89,10 @@ def test_noalloc_matches_the_handle_path_twice(M):
         u_s = d_u0_s.cpu().numpy()
         U_h = ctl.unew()
         U_s = d_Unew.cpu().numpy()
-        assert np.max(np.abs(u_s[:4] - u_h[:4])) <= U_TOL, (call, u_s, u_h)
-        assert np.max(np.abs(U_s[:, :4] - U_h[:, :4])) <= U_TOL, call
+        assert np.max(np.abs(u_s[:nu] - u_h[:nu])) <= U_TOL, (call, u_s, u_h)
+        assert np.max(np.abs(U_s[:, :nu] - U_h[:, :nu])) <= U_TOL, call
         # warm start for the next call: shift by one row, repeat the last
-        d_U = torch.cat([d_Unew[1:], d_Unew[-1:]], dim=0).contiguous()
+        U = np.vstack([U_s[1:], U_s[-1:]]).astype(np.float32)
     ctl.close()
 
 
