@@ -21,7 +21,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # rollout kernel: 96 registers so that five 128-thread blocks fit on an SM
 # (measured: 2.44 ms per 256-drone batched step vs 2.54 ms at 128 or 80)
 DEFAULT_DEFINES = ("MPPI_ROLLOUT_MIN_BLOCKS=5",)
-SOURCES = ["mppi_kernels.cu", "mppi_api.cu", "mppi_serve.cu", "mppi_noalloc.cu"]
+SOURCES = ["mppi_rollout_gate.cu", "mppi_rollout_contour.cu", "mppi_rollout_track.cu", "mppi_kernels.cu",
+           "mppi_api.cu", "mppi_serve.cu", "mppi_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -40,6 +40,16 @@ cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles,
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
                            int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor);
 cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s);
+// the rollout kernel's instances, one translation unit per objective
+cudaError_t configure_rollout_gate();
+cudaError_t configure_rollout_contour();
+cudaError_t configure_rollout_track();
+cudaError_t launch_rollout_gate(int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
+                                uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor);
+cudaError_t launch_rollout_contour(int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
+                                   uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor);
+cudaError_t launch_rollout_track(int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles, int block,
+                                 uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
                           uint32_t* out, cudaStream_t s);
 cudaError_t launch_normals(uint32_t seed, uint32_t drone, uint32_t k, uint32_t it, uint32_t blk, int n, float* out,
