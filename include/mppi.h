@@ -67,8 +67,15 @@ enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
  *           the diagnostics;
  *   REGEN:  the rollout draws them and the update draws them again; nothing
  *           is stored (no noise memory: mppi_get_noise / mppi_set_noise
- *           return MPPI_ERR_ARG; needs MPPI_NOISE_F32). */
-enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1, MPPI_NOISEGEN_REGEN = 2 };
+ *           return MPPI_ERR_ARG; needs MPPI_NOISE_F32);
+ *   SMEM:   the rollout draws them and keeps its block's normals in shared
+ *           memory, where the update reads them: one launch, no noise memory
+ *           and no round trip to L2 in the update.  For small, latency-bound
+ *           solves: the block needs 16 N_cap x (block x samples_per_thread)
+ *           bytes more shared memory (20 for contouring), at most 200 KB
+ *           in all (MPPI_ERR_ARG beyond); mppi_get_noise / mppi_set_noise
+ *           return MPPI_ERR_ARG. */
+enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1, MPPI_NOISEGEN_REGEN = 2, MPPI_NOISEGEN_SMEM = 3 };
 /* accumulation of the K-sample weighted update sum (Eq. 5) */
 enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
 enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };

@@ -210,7 +210,7 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   if (p->noise_dtype != MPPI_NOISE_F32 && p->noise_dtype != MPPI_NOISE_BF16)
     return fail(MPPI_ERR_ARG, "unknown noise dtype");
   if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
-  if (p->noise_gen < MPPI_NOISEGEN_KERNEL || p->noise_gen > MPPI_NOISEGEN_REGEN)
+  if (p->noise_gen < MPPI_NOISEGEN_KERNEL || p->noise_gen > MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p->noise_gen == MPPI_NOISEGEN_REGEN && p->noise_dtype != MPPI_NOISE_F32)
     return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
@@ -222,6 +222,15 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
     return fail(MPPI_ERR_ARG, "block %d must be a multiple of 32 in [32, %d]", blk, rollout_max_block());
   if (p->samples_per_thread < 0 || p->samples_per_thread > MPPI_MAX_SPT)
     return fail(MPPI_ERR_ARG, "samples_per_thread %d outside [0, %d]", p->samples_per_thread, MPPI_MAX_SPT);
+  if (p->noise_gen == MPPI_NOISEGEN_SMEM) {
+    const int tile = blk * (p->samples_per_thread ? p->samples_per_thread : 1);
+    const int Nc = p->N_cap ? p->N_cap : p->N, Kc = p->K_cap ? p->K_cap : p->K;
+    const uint32_t need = rollout_smem_bytes(Nc, p->objective, t->S, tile, std::max(32, (Kc + tile - 1) / tile),
+                                             MPPI_NOISEGEN_SMEM);
+    if (need > kRolloutSmemMax)
+      return fail(MPPI_ERR_ARG, "noise kept in shared memory needs %u bytes per block, more than %u", need,
+                  kRolloutSmemMax);
+  }
   if (t->n_gates < 0 || t->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p->objective == MPPI_OBJ_GATE && (t->n_gates < 1 || !t->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs at least one gate");
@@ -247,7 +256,7 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
   const int Gn = 2 * sq + 16;  // >= n_groups_for(T) for every T <= T_cap
   const bool bf16 = p->noise_dtype == MPPI_NOISE_BF16;
   const bool five = p->objective == MPPI_OBJ_CONTOUR;
-  const bool stored = p->noise_gen != MPPI_NOISEGEN_REGEN;
+  const bool stored = p->noise_gen != MPPI_NOISEGEN_REGEN && p->noise_gen != MPPI_NOISEGEN_SMEM;
   Slab s;
   Sizes z;
   z.off_desc = s.take(sizeof(SolveDesc));
@@ -535,7 +544,8 @@ int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mp
   d.ref = reinterpret_cast<float*>(b + z.off_ref);
   d.T = track->T;
   d.dt_ref = track->dt_ref;
-  const bool bf16 = d.noise_bf16, stored = d.noise_gen != MPPI_NOISEGEN_REGEN;
+  const bool bf16 = d.noise_bf16,
+             stored = d.noise_gen != MPPI_NOISEGEN_REGEN && d.noise_gen != MPPI_NOISEGEN_SMEM;
   d.Z4 = (stored && !bf16) ? reinterpret_cast<float4*>(b + z.off_Z) : nullptr;
   d.Zb = (stored && bf16) ? reinterpret_cast<uint2*>(b + z.off_Z) : nullptr;
   d.Z5 = (stored && !bf16 && h->nu == 5) ? reinterpret_cast<float*>(b + z.off_Z5) : nullptr;
@@ -649,7 +659,7 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   } else {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
   }
-  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles));
+  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles), gen);
   CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen,
                     d.rotor));
   return MPPI_OK;
@@ -734,7 +744,8 @@ int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass) {
 int mppi_get_noise(mppi_handle h, float* Z) {
   if (!h || !Z) return fail(MPPI_ERR_ARG, "null argument");
   const SolveDesc& d = h->hd;
-  if (d.noise_gen == MPPI_NOISEGEN_REGEN) return fail(MPPI_ERR_ARG, "regenerated noise is not stored");
+  if (d.noise_gen == MPPI_NOISEGEN_REGEN || d.noise_gen == MPPI_NOISEGEN_SMEM)
+    return fail(MPPI_ERR_ARG, "this handle keeps no noise in device memory");
   const size_t nk = (size_t)d.N * d.K;
   std::vector<float> z4(nk * 4), z5(h->nu == 5 ? nk : 0);
   if (d.noise_bf16) {
@@ -869,7 +880,8 @@ int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* strea
   if (h->nu == 5 && !d_Z5) return fail(MPPI_ERR_ARG, "contouring needs the 5th noise column");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SolveDesc& d = h->hd;
-  if (d.noise_gen == MPPI_NOISEGEN_REGEN) return fail(MPPI_ERR_ARG, "a regenerating handle has no noise buffer");
+  if (d.noise_gen == MPPI_NOISEGEN_REGEN || d.noise_gen == MPPI_NOISEGEN_SMEM)
+    return fail(MPPI_ERR_ARG, "this handle has no noise buffer");
   const size_t nk = (size_t)d.N * d.K;
   const size_t el = d.noise_bf16 ? 2 : 4;
   void* z4 = d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4;
@@ -1075,7 +1087,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     int gi = find(rg, k);
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
     rsmem[gi] =
-        std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles)));
+        std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles),
+                                               d.noise_gen));
     const int gn = d.noise_gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
       rg[gi].second.push_back(Tile{i, t * tile_samples(d)});

@@ -14,8 +14,8 @@
 
 namespace mppi {
 
-uint32_t rollout_smem_bytes(int N, int objective, int S, int tile, int merge_cap) {
-  return smem_layout(N, objective, S, tile, merge_cap, path_fits_smem(S)).total;
+uint32_t rollout_smem_bytes(int N, int objective, int S, int tile, int merge_cap, int gen) {
+  return smem_layout(N, objective, S, tile, merge_cap, path_fits_smem(S), gen).total;
 }
 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }

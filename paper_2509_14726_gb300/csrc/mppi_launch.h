@@ -20,7 +20,10 @@ __host__ __device__ inline int n_groups_for(int T) {
 }
 
 __host__ __device__ int path_fits_smem(int S);
-uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap);
+// dynamic shared memory of a rollout launch (gen: MPPI_NOISEGEN_*)
+uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap, int gen);
+// largest dynamic shared memory a rollout launch may use
+constexpr uint32_t kRolloutSmemMax = 200 * 1024;
 unsigned long long launches_so_far();
 void add_launches(int n);  // kernels run by a graph launch
 // model, sampling and cost fields of a descriptor from the C-ABI structs

@@ -11,6 +11,7 @@
 // noise, costs, tile partials, merge tickets) in one file-scope device array
 // of fixed size that is loaded with the library.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -133,7 +134,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (block < 32 || block > kMaxBlock || block % 32) return fail(MPPI_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
   if (p.K < 1 || p.N < 1 || p.N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K or N out of range");
   if (!(p.dt > 0) || !(p.lambda > 0)) return fail(MPPI_ERR_ARG, "dt and lambda must be positive");
-  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_REGEN)
+  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32)
     return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
@@ -141,6 +142,12 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
     return fail(MPPI_ERR_ARG, "samples_per_thread out of range");
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
+  if (p.noise_gen == MPPI_NOISEGEN_SMEM) {
+    const int tile = block * (p.samples_per_thread ? p.samples_per_thread : 1);
+    if (rollout_smem_bytes(p.N, p.objective, d_track->S, tile, std::max(32, (p.K + tile - 1) / tile),
+                           MPPI_NOISEGEN_SMEM) > kRolloutSmemMax)
+      return fail(MPPI_ERR_ARG, "noise kept in shared memory does not fit a block's shared memory");
+  }
   if (gate < 0) return fail(MPPI_ERR_ARG, "gate index is negative");
   if (p.objective == MPPI_OBJ_GATE && (d_track->n_gates < 1 || !d_track->gates))
     return fail(MPPI_ERR_ARG, "gate objective needs gates");
@@ -150,7 +157,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
     return fail(MPPI_ERR_ARG, "tracking needs a reference table");
   const int five = p.objective == MPPI_OBJ_CONTOUR;
   const int bf16 = p.noise_dtype == MPPI_NOISE_BF16;
-  const bool stored = p.noise_gen != MPPI_NOISEGEN_REGEN;  // regenerated noise needs no buffer
+  // regenerated noise and noise kept in shared memory need no buffer
+  const bool stored = p.noise_gen != MPPI_NOISEGEN_REGEN && p.noise_gen != MPPI_NOISEGEN_SMEM;
   const Layout L = layout_for(p.K, p.N, block, five, bf16, stored);
   if (L.total > kScratchBytes) {
     char buf[200];
@@ -224,7 +232,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.u0 = d_u0;
   io.status = nullptr;
   const uint32_t smem =
-      rollout_smem_bytes(p.N, p.objective, d.S, tile_samples(d), d.n_tiles > 32 ? d.n_tiles : 32);
+      rollout_smem_bytes(p.N, p.objective, d.S, tile_samples(d), d.n_tiles > 32 ? d.n_tiles : 32, p.noise_gen);
   if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen, d.rotor) !=
       cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");

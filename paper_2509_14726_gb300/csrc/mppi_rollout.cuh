@@ -199,14 +199,15 @@ __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
 // shared-memory layout of the rollout kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_j, off_merge, total;
+  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_j, off_merge, off_z, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-// tile: samples per tile (threads per block x samples per thread)
+// tile: samples per tile (threads per block x samples per thread); gen: where
+// the normals are drawn (MPPI_NOISEGEN_SMEM keeps the tile's normals here)
 __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, int tile, int merge_cap,
-                                                  int path_in_smem) {
+                                                  int path_in_smem, int gen) {
   SmemLayout L;
   uint32_t o = 0;
   L.off_U = o;
@@ -225,6 +226,9 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
   o += align16((uint32_t)tile * 8u);
   L.off_merge = o;
   o += align16((uint32_t)merge_cap * 8u);
+  L.off_z = o;  // [N][tile] float4 normals, then [N][tile] 5th normals (contouring)
+  if (gen == MPPI_NOISEGEN_SMEM)
+    o += align16((uint32_t)N * tile * 16u) + (objective == MPPI_OBJ_CONTOUR ? align16((uint32_t)N * tile * 4u) : 0u);
   L.total = o;
   return L;
 }
@@ -321,17 +325,26 @@ __device__ inline void merge_partials(const SolveDesc& d, const MergeIn in, int 
       add2(sh, sl, p, fmaf(Si.x, sc, -p) + Si.y * sc);
     }
     block_sum2_f(sh, sl, redf);  // its barriers make scale_f visible
+    // partials are requested 8 at a time (one L2 round trip per 8 instead of
+    // per partial) and summed in index order
+    auto acc_one = [&](float& hi, float& lo, float2 v, float sc) {
+      const float p = v.x * sc;
+      float t, e;
+      two_sum(hi, p, t, e);
+      hi = t;
+      lo += e + fmaf(v.x, sc, -p) + v.y * sc;
+    };
     for (int o = threadIdx.x; o < NNU; o += blockDim.x) {
       float hi = 0.f, lo = 0.f;
-      for (int i = 0; i < n; ++i) {
-        const float2 v = unpack2(__ldcg(in.P + (size_t)i * NNU + o));
-        const float sc = scale_f[i];
-        const float p = v.x * sc;
-        float t, e;
-        two_sum(hi, p, t, e);
-        hi = t;
-        lo += e + fmaf(v.x, sc, -p) + v.y * sc;
+      int i = 0;
+      for (; i + 8 <= n; i += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = unpack2(__ldcg(in.P + (size_t)(i + t) * NNU + o));
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc_one(hi, lo, v[t], scale_f[i + t]);
       }
+      for (; i < n; ++i) acc_one(hi, lo, unpack2(__ldcg(in.P + (size_t)i * NNU + o)), scale_f[i]);
       float t, e;
       two_sum(hi, lo, t, e);
       out_P[o] = pack2(t, e);
@@ -356,7 +369,15 @@ __device__ inline void merge_partials(const SolveDesc& d, const MergeIn in, int 
   for (int o = threadIdx.x; o < NNU; o += blockDim.x) {
     if (f64) {
       double acc = 0.0;
-      for (int i = 0; i < n; ++i) acc = fma(__ldcg(in.P + (size_t)i * NNU + o), scale_s[i], acc);
+      int i = 0;
+      for (; i + 8 <= n; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = __ldcg(in.P + (size_t)(i + t) * NNU + o);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc = fma(v[t], scale_s[i + t], acc);
+      }
+      for (; i < n; ++i) acc = fma(__ldcg(in.P + (size_t)i * NNU + o), scale_s[i], acc);
       out_P[o] = acc;
     } else {
       float hi = 0.f, lo = 0.f;
@@ -423,7 +444,8 @@ static_assert(MPPI_EPI_LANES >= 1 && MPPI_EPI_LANES <= 32 && (MPPI_EPI_LANES & (
 // Kahan step (the chain's rounding is a few ulps of its own few terms).
 template <int ACC, int BF16, int GEN>
 __device__ __forceinline__ void eq5_rows(const SolveDesc& d, const float* sU, const float* sE, uint32_t iter,
-                                         int m0, int nvalid, double* myP) {
+                                         int m0, int nvalid, double* myP, const float4* sZ4, const float* sZ5,
+                                         int TS) {
   constexpr int kEpiLanes = MPPI_EPI_LANES, kEpiRows = 32 / kEpiLanes, kEpiBatch = GEN == 2 ? 1 : MPPI_EPI_BATCH;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   const int sub = lane / kEpiLanes, sl = lane % kEpiLanes;
@@ -456,10 +478,15 @@ __device__ __forceinline__ void eq5_rows(const SolveDesc& d, const float* sU, co
         for (int t = 0; t < kEpiBatch; ++t) {
           const int ic = min(i0 + t * kEpiLanes, nvalid - 1);  // in range; weight 0 past nvalid
           wb[t] = i0 + t * kEpiLanes < nvalid ? sE[ic] : 0.f;
-          if (GEN == 2)
+          if (GEN == 3) {
+            const float4 v = sZ4[(size_t)k * TS + ic];
+            zb[t][0] = v.x; zb[t][1] = v.y; zb[t][2] = v.z; zb[t][3] = v.w;
+            zb[t][4] = five ? sZ5[(size_t)k * TS + ic] : 0.f;
+          } else if (GEN == 2) {
             gen_noise<BF16, false>(d, iter, m0 + ic, k, zb[t], five);
-          else
+          } else {
             load_noise<BF16, GEN == 0>(d, (size_t)k * K + m0 + ic, zb[t], five);
+          }
         }
         float part[kNU];
 #pragma unroll
@@ -552,7 +579,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const int path_smem = path_fits_smem(d.S);
   // the tile: TS = B spt samples; thread tid runs m0 + tid + rep B, rep < spt
   const int spt = d.spt, TS = B * spt;
-  const SmemLayout Ls = smem_layout(N, OBJ, d.S, TS, max(d.n_tiles, 32), path_smem);
+  const SmemLayout Ls = smem_layout(N, OBJ, d.S, TS, max(d.n_tiles, 32), path_smem, GEN);
+  // GEN 3: the tile's normals, kept here for the update (Eq. 5)
+  float4* sZ4 = reinterpret_cast<float4*>(smem + Ls.off_z);
+  float* sZ5 = reinterpret_cast<float*>(smem + Ls.off_z + align16((uint32_t)N * TS * 16u));
   float* sU = reinterpret_cast<float*>(smem + Ls.off_U);
   int* sPrev = reinterpret_cast<int*>(smem + Ls.off_prev);
   GateF* sG = reinterpret_cast<GateF*>(smem + Ls.off_gates);
@@ -579,8 +609,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     if (bytes_path) bulk_g2s(sPath, d.path, bytes_path, &mbar);
   }
   DevState* st = d.st;
-  // GEN != 0: the normals are drawn here (GEN 1 stores them, GEN 2 draws them
-  // again in the epilogue) instead of being loaded from the noise kernel's output
+  // GEN != 0: the normals are drawn here (GEN 1 stores them in global memory,
+  // GEN 2 draws them again in the epilogue, GEN 3 keeps them in shared
+  // memory) instead of being loaded from the noise kernel's output
   const uint32_t iter = GEN ? st->iter : 0u;
   // gate frames (computed here from the raw table: centre, yaw, half sizes)
   if (OBJ == MPPI_OBJ_GATE) {
@@ -773,10 +804,15 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       // loop invariants in registers (the descriptor lives in shared memory)
       // software pipeline: the next step's noise is in flight during this step
       float z[kNU], zn[kNU];
+      const int it = tid + rep * B;  // the sample's place in the tile
       if (GEN)
         gen_noise<BF16, GEN == 1>(d, iter, m, 0, zn, five);
       else
         load_noise<BF16>(d, (size_t)m, zn, five);
+      if (GEN == 3) {
+        sZ4[it] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+        if (five) sZ5[it] = zn[4];
+      }
 #pragma unroll kRolloutUnroll
       for (int k = 0; k < N; ++k) {
 #pragma unroll
@@ -786,6 +822,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
             gen_noise<BF16, GEN == 1>(d, iter, m, k + 1, zn, five);
           else
             load_noise<BF16>(d, (size_t)(k + 1) * K + m, zn, five);
+          if (GEN == 3) {
+            sZ4[(size_t)(k + 1) * TS + it] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+            if (five) sZ5[(size_t)(k + 1) * TS + it] = zn[4];
+          }
         }
         const float* Uk = sU + kNU * k;
         // sampling (Eq. 3 with the clamp): sigma and the input bounds are
@@ -1004,9 +1044,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const int tile_in_solve = tile.m0 / TS;
   double* myP = d.part_P + (size_t)tile_in_solve * NNU;
   switch (acc) {
-    case MPPI_ACC_F64: eq5_rows<MPPI_ACC_F64, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
-    case MPPI_ACC_F32: eq5_rows<MPPI_ACC_F32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
-    default: eq5_rows<MPPI_ACC_KAHAN32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP); break;
+    case MPPI_ACC_F64: eq5_rows<MPPI_ACC_F64, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP, sZ4, sZ5, TS); break;
+    case MPPI_ACC_F32: eq5_rows<MPPI_ACC_F32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP, sZ4, sZ5, TS); break;
+    default: eq5_rows<MPPI_ACC_KAHAN32, BF16, GEN>(d, sU, sE, iter, tile.m0, nvalid, myP, sZ4, sZ5, TS); break;
   }
   if (tid == 0) {
     d.part_m[tile_in_solve] = m_t;
@@ -1154,6 +1194,9 @@ cudaError_t configure_rollout_t() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(rollout_kernel<OBJ, 0, 2, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_kernel<OBJ, BF16, 3, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
   return e;
 }
 
@@ -1170,7 +1213,9 @@ template <int OBJ, int BF16, int ROT>
 cudaError_t launch_rollout_t(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, uint32_t smem,
                              LaunchIO io, cudaStream_t s, int gen) {
   (void)cudaGetLastError();
-  if (gen == 2) {
+  if (gen == 3) {
+    rollout_kernel<OBJ, BF16, 3, ROT><<<n_tiles, block, smem, s>>>(descs, tiles, io);
+  } else if (gen == 2) {
     if constexpr (BF16) return cudaErrorInvalidValue;
     else rollout_kernel<OBJ, 0, 2, ROT><<<n_tiles, block, smem, s>>>(descs, tiles, io);
   } else if (gen == 1) {

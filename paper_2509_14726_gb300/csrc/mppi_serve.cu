@@ -137,7 +137,8 @@ Scratch scratch_for(int K, int N, int block, int five, int bf16, int gen) {
     o = al256(o + b);
     return r;
   };
-  const bool stored = gen != MPPI_NOISEGEN_REGEN;  // regenerated noise needs no buffer
+  // regenerated noise and noise kept in shared memory need no buffer
+  const bool stored = gen != MPPI_NOISEGEN_REGEN && gen != MPPI_NOISEGEN_SMEM;
   s.Z = take(stored ? (size_t)N * K * (bf16 ? 8 : 16) : 16);
   s.Z5 = take(five && stored ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
   s.J = take(sizeof(double) * K);
@@ -308,9 +309,15 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   if (p.objective < 0 || p.objective > 2) return sfail(MPPI_ERR_ARG, "unknown objective");
   if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return sfail(MPPI_ERR_ARG, "noise dtype");
   if (p.accum < 0 || p.accum > 2) return sfail(MPPI_ERR_ARG, "unknown accumulation mode");
-  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_REGEN ||
+  if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_SMEM ||
       (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32))
     return sfail(MPPI_ERR_ARG, "bad noise generation mode");
+  if (p.noise_gen == MPPI_NOISEGEN_SMEM) {
+    const int tile = block * (p.samples_per_thread ? p.samples_per_thread : 1);
+    if (rollout_smem_bytes(N_cap, p.objective, track->S, tile, std::max(32, (K_cap + tile - 1) / tile),
+                           MPPI_NOISEGEN_SMEM) > kRolloutSmemMax)
+      return sfail(MPPI_ERR_ARG, "noise kept in shared memory does not fit a block's shared memory");
+  }
   if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
     return sfail(MPPI_ERR_ARG, "samples_per_thread outside [0, %d]", MPPI_MAX_SPT);
   if (track->n_gates < 0 || track->n_gates > MPPI_MAX_GATES) return sfail(MPPI_ERR_ARG, "n_gates out of range");
@@ -507,7 +514,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     dd.K = r.K;
     dd.N = r.N;
     dd.n_tiles = (r.K + tile_samples(dd) - 1) / tile_samples(dd);
-    const bool stored = dd.noise_gen != MPPI_NOISEGEN_REGEN;
+    const bool stored = dd.noise_gen != MPPI_NOISEGEN_REGEN && dd.noise_gen != MPPI_NOISEGEN_SMEM;
     dd.Z4 = (stored && !dd.noise_bf16) ? reinterpret_cast<float4*>(b + sc.Z) : nullptr;
     dd.Zb = (stored && dd.noise_bf16) ? reinterpret_cast<uint2*>(b + sc.Z) : nullptr;
     dd.Z5 = (stored && d.nu == 5 && !dd.noise_bf16) ? reinterpret_cast<float*>(b + sc.Z5) : nullptr;
@@ -548,7 +555,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * tile_samples(dd)});
     groups[g].smem = std::max(groups[g].smem, rollout_smem_bytes(dd.N, dd.objective, dd.S, tile_samples(dd),
-                                                                 dd.n_tiles > 32 ? dd.n_tiles : 32));
+                                                                 dd.n_tiles > 32 ? dd.n_tiles : 32, dd.noise_gen));
     if (dd.objective == MPPI_OBJ_GATE) which.push_back(i);
   }
   Tile* htiles = reinterpret_cast<Tile*>(sl.host + st.tiles);

@@ -64,7 +64,7 @@ def _same(a, b):
     np.testing.assert_array_equal(a.costs(), b.costs())
     np.testing.assert_array_equal(a.unew(), b.unew())
     np.testing.assert_array_equal(a.nominal(), b.nominal())
-    if a.params.noise_gen != 2:
+    if a.params.noise_gen in (0, 1):
         np.testing.assert_array_equal(a.noise(), b.noise())
     assert a.export_state() == b.export_state()
 
@@ -72,7 +72,7 @@ def _same(a, b):
 def _close(a, b):
     """Same noise bit for bit (where a stores it); costs and update to
     binary32 rounding."""
-    if a.params.noise_gen != 2:
+    if a.params.noise_gen in (0, 1):
         np.testing.assert_array_equal(a.noise(), b.noise())
     na, fa = a.sample_info()
     nb, fb = b.sample_info()
@@ -85,7 +85,7 @@ def _close(a, b):
     assert np.abs(a.nominal() - b.nominal()).max() <= U_ABS_TOL
 
 
-GEN_CASES = [(1, 0), (1, 1), (2, 0)]  # (noise generation, bf16 storage)
+GEN_CASES = [(1, 0), (1, 1), (2, 0), (3, 0), (3, 1)]  # (noise generation, bf16 storage)
 
 
 @pytest.mark.parametrize("objective", [0, 1, 2])
@@ -109,16 +109,16 @@ def test_drawn_in_rollout_matches_separate(O, M, objective, gen, bf16, K, N, blo
 
 
 @pytest.mark.parametrize("objective", [0, 1, 2])
-@pytest.mark.parametrize("gen", [1, 2])
+@pytest.mark.parametrize("gen", [1, 2, 3])
 def test_drawn_in_rollout_against_oracle(O, M, objective, gen):
-    case = _case(objective, 4096, 50)
+    case = _case(objective, 4096, 50 if gen != 3 else 20)
     gpu, ora = make_pair(case, noise_gen=gen)
     t0 = 0.37
     x0 = _x0(O, case, t0)
     gpu.solve(x0, t0)
     r = ora.solve(x0, t0)
     compare(gpu, r, f"noise generation {gen}, objective {objective}")
-    if gen == 2:
+    if gen in (2, 3):
         gpu.close()
         return
     # the stored normals are the oracle's Philox / Box-Muller draws
@@ -138,7 +138,7 @@ def test_batch_with_mixed_noise_modes(M, use_graph):
     for i, it in enumerate(items):
         sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id)
         case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
-        mode = i % 3  # separate pass, fused, regenerated
+        mode = i % 4  # separate pass, fused, regenerated, kept in shared memory
         g1 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         g2 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         trip.append((g1, g2, case))
@@ -229,6 +229,25 @@ def test_regenerated_noise_has_no_buffer(M):
         M.mppi_set_noise(a.h, z.data_ptr(), z.data_ptr())
     with pytest.raises(M.MppiError) as e:
         M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_REGEN, noise_dtype=M.NOISE_BF16)
+    assert e.value.code == M.MPPI_ERR_ARG
+    a.close()
+    b.close()
+
+
+def test_noise_kept_in_shared_memory(M):
+    """MPPI_NOISEGEN_SMEM needs no noise buffer and refuses the noise getters;
+    a horizon whose normals do not fit a block's shared memory is refused at
+    creation."""
+    case = _case(0, 2048, 20)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_SMEM)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL)
+    assert M.mppi_device_bytes(b.h) - M.mppi_device_bytes(a.h) >= 2048 * 20 * 16 - 512
+    with pytest.raises(M.MppiError) as e:
+        a.noise()
+    assert e.value.code == M.MPPI_ERR_ARG
+    big = _case(1, 2048, 128)
+    with pytest.raises(M.MppiError) as e:
+        M.Controller(big.mc, big.sc, big.tr, noise_gen=M.NOISEGEN_SMEM)
     assert e.value.code == M.MPPI_ERR_ARG
     a.close()
     b.close()
