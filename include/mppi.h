@@ -411,6 +411,14 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
  * the n is queued then). */
 int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const float* x0s, const double* t0s,
                        const int32_t* Ks, const int32_t* Ns, int64_t* ids_out);
+/* The same with a deadline per request (host array [n] of mppi_clock()
+ * times; 0 = none): a request still queued at its deadline is not launched
+ * but dropped (load shedding: a controller gains nothing from a solve whose
+ * control period has passed).  Dropped requests come back from
+ * mppi_server_poll with status MPPI_ERR_NOT_ADMITTED and t_launch 0. */
+int mppi_server_submit_deadline(mppi_server s, int32_t n, const int32_t* drones, const float* x0s,
+                                const double* t0s, const int32_t* Ks, const int32_t* Ns, const double* deadlines,
+                                int64_t* ids_out);
 /* Admits and launches at most one batch if a slot is free; writes how many
  * requests it launched (0 if none could be admitted).  If the transfer or a
  * launch of the batch fails, the admitted requests are handed back (scratch

@@ -117,6 +117,7 @@ struct Request {
   double t0;
   int32_t K, N;
   double t_submit, t_launch;
+  double deadline = 0.0;      // mppi_clock() after which it is not launched (0: none)
   size_t off = 0, bytes = 0;  // scratch in the pool
 };
 
@@ -172,6 +173,7 @@ struct Slot {
 struct mppi_server_s {
   int device = 0;
   int max_drones = 0, max_batch = 0, max_tiles = 0;
+  double refused = 0.0;  // requests dropped past their deadline
   bool fail_next_launch = false;  // testing hook: the next admitted batch fails on the host
   std::vector<Drone> drones;
   char* pool_base = nullptr;
@@ -405,6 +407,12 @@ extern "C" {
 
 int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const float* x0s, const double* t0s,
                        const int32_t* Ks, const int32_t* Ns, int64_t* ids_out) {
+  return mppi_server_submit_deadline(s, n, drones, x0s, t0s, Ks, Ns, nullptr, ids_out);
+}
+
+int mppi_server_submit_deadline(mppi_server s, int32_t n, const int32_t* drones, const float* x0s,
+                                const double* t0s, const int32_t* Ks, const int32_t* Ns, const double* deadlines,
+                                int64_t* ids_out) {
   if (!s || n < 0 || (n > 0 && (!drones || !x0s || !Ks || !Ns))) return sfail(MPPI_ERR_ARG, "null argument");
   std::lock_guard<std::mutex> lk(s->mu);
   for (int i = 0; i < n; ++i) {
@@ -430,6 +438,7 @@ int mppi_server_submit(mppi_server s, int32_t n, const int32_t* drones, const fl
     r.N = Ns[i];
     r.t_submit = t;
     r.t_launch = 0.0;
+    r.deadline = deadlines ? deadlines[i] : 0.0;
     s->queue.push_back(r);
     if (ids_out) ids_out[i] = r.id;
   }
@@ -456,9 +465,25 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   std::deque<Request> keep;
   int tiles = 0;
   bool blocked = false;
+  const double t_adm = now_s();
   while (!s->queue.empty()) {
     Request r = s->queue.front();
     s->queue.pop_front();
+    if (r.deadline > 0.0 && t_adm > r.deadline) {
+      // past its deadline before it could be launched: refused, reported by poll
+      mppi_result_t res;
+      memset(&res, 0, sizeof res);
+      res.request = r.id;
+      res.drone = r.drone;
+      res.status = MPPI_ERR_NOT_ADMITTED;
+      res.K = r.K;
+      res.N = r.N;
+      res.t_submit = r.t_submit;
+      res.t_done = t_adm;
+      s->done.push_back(res);
+      s->refused += 1.0;
+      continue;
+    }
     Drone& d = s->drones[r.drone];
     const int TS = d.block * d.hd.spt;
     const int T = (r.K + TS - 1) / TS;

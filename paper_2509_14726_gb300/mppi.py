@@ -109,6 +109,7 @@ def load():
         "mppi_server_create": ([I32, sz, I32, I32, C.POINTER(vp)], C.c_int),
         "mppi_server_add_drone": ([vp, C.POINTER(Model), C.POINTER(Params), C.POINTER(TrackC), C.POINTER(I32)], C.c_int),
         "mppi_server_submit": ([vp, I32, vp, vp, vp, vp, vp, vp], C.c_int),
+        "mppi_server_submit_deadline": ([vp, I32, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "mppi_server_step": ([vp, C.POINTER(I32)], C.c_int),
         "mppi_server_poll": ([vp, vp, I32, C.POINTER(I32)], C.c_int),
         "mppi_server_stats": ([vp, C.POINTER(C.c_double)], C.c_int),
@@ -586,7 +587,9 @@ class Server:
                                             C.byref(tables.c), C.byref(d)))
         return int(d.value)
 
-    def submit(self, drones, x0s, t0s, Ks, Ns) -> np.ndarray:
+    def submit(self, drones, x0s, t0s, Ks, Ns, deadlines=None) -> np.ndarray:
+        """Queues requests; deadlines (mppi_clock() times, optional): a
+        request still queued then is dropped (status MPPI_ERR_NOT_ADMITTED)."""
         n = len(drones)
         dr = np.ascontiguousarray(drones, np.int32)
         x = _f32(np.asarray(x0s).reshape(n, 13))
@@ -594,8 +597,14 @@ class Server:
         k = np.ascontiguousarray(Ks, np.int32)
         nn = np.ascontiguousarray(Ns, np.int32)
         ids = np.zeros(n, np.int64)
-        _check(load().mppi_server_submit(C.c_void_p(self.h), n, dr.ctypes.data, x.ctypes.data, t.ctypes.data,
-                                         k.ctypes.data, nn.ctypes.data, ids.ctypes.data))
+        if deadlines is None:
+            _check(load().mppi_server_submit(C.c_void_p(self.h), n, dr.ctypes.data, x.ctypes.data, t.ctypes.data,
+                                             k.ctypes.data, nn.ctypes.data, ids.ctypes.data))
+        else:
+            dl = np.ascontiguousarray(deadlines, np.float64)
+            _check(load().mppi_server_submit_deadline(C.c_void_p(self.h), n, dr.ctypes.data, x.ctypes.data,
+                                                      t.ctypes.data, k.ctypes.data, nn.ctypes.data, dl.ctypes.data,
+                                                      ids.ctypes.data))
         return ids
 
     def step(self) -> int:

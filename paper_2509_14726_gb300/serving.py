@@ -12,7 +12,11 @@ rate down), against
   handles (one solve per launch sequence).
 
 Latency of a request = time its result is available on the host - its
-scheduled arrival time.  Both paths see the same arrival schedule.
+scheduled arrival time.  Both paths see the same arrival schedule.  With a
+deadline of d control periods, a request that has not started d periods after
+its arrival is refused (load shedding: its drone has already moved on); the
+served path leaves that to the server (mppi_server_submit_deadline), the plain
+path skips it.
 """
 from __future__ import annotations
 
@@ -32,6 +36,7 @@ class Schedule:
     drone: np.ndarray    # drone index
     K: np.ndarray
     N: np.ndarray
+    period: np.ndarray   # the requesting drone's control period (wall clock), s
 
 
 def make_schedule(fleet: Sequence[W.ServeDrone], duration_s: float, time_scale: float, K_choices, N_choices,
@@ -49,7 +54,8 @@ def make_schedule(fleet: Sequence[W.ServeDrone], duration_s: float, time_scale: 
     n = len(t)
     K = rng.choice(np.asarray(K_choices, np.int32), n)
     N = rng.choice(np.asarray(N_choices, np.int32), n)
-    return Schedule(t[order], dr[order], K, N)
+    period = np.array([1.0 / (fleet[i].rate_hz * time_scale) for i in dr[order]])
+    return Schedule(t[order], dr[order], K, N, period)
 
 
 def _stats(lat: np.ndarray, done: int, wall: float, steps: float) -> dict:
@@ -60,10 +66,19 @@ def _stats(lat: np.ndarray, done: int, wall: float, steps: float) -> dict:
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3)}
 
 
+def _load(out: dict, n: int, refused: int, window: float) -> dict:
+    """Offered, achieved and refused request rates over the arrival window."""
+    out.update({"offered": n, "offered_per_s": n / window, "achieved_per_s": out.get("finished", 0) / window,
+                "refused": int(refused), "refused_per_s": refused / window})
+    return out
+
+
 def run_served(fleet, sched: Schedule, budget_bytes: int = 40 << 30, n_slots: int = 3, max_batch: int = 512,
                K_cap: int = 16384, N_cap: int = 80, dt: float = 0.02, drain_s: float = 30.0,
-               max_inflight_s: Optional[float] = None) -> dict:
-    """Replays the schedule against one mppi_server; returns latency statistics."""
+               deadline_periods: Optional[float] = None) -> dict:
+    """Replays the schedule against one mppi_server; returns latency
+    statistics of the served requests and the offered / achieved / refused
+    rates (refusals only with deadline_periods)."""
     srv = M.Server(len(fleet), budget_bytes, n_slots, max_batch)
     ids = []
     for d in fleet:
@@ -77,6 +92,7 @@ def run_served(fleet, sched: Schedule, budget_bytes: int = 40 << 30, n_slots: in
     t_start = M.mppi_clock()
     i = 0
     finished = 0
+    refused = 0
     id_to_idx = {}
     steps_done = 0.0
     while finished < n:
@@ -84,7 +100,10 @@ def run_served(fleet, sched: Schedule, budget_bytes: int = 40 << 30, n_slots: in
         j = int(np.searchsorted(sched.t, now, side="right"))
         if j > i:
             sl = slice(i, j)
-            got = srv.submit(sched.drone[sl], X0[sched.drone[sl]], sched.t[sl], sched.K[sl], sched.N[sl])
+            dl = None
+            if deadline_periods is not None:
+                dl = t_start + sched.t[sl] + deadline_periods * sched.period[sl]
+            got = srv.submit(sched.drone[sl], X0[sched.drone[sl]], sched.t[sl], sched.K[sl], sched.N[sl], dl)
             for q, rid in enumerate(got):
                 id_to_idx[int(rid)] = i + q
             i = j
@@ -93,6 +112,9 @@ def run_served(fleet, sched: Schedule, budget_bytes: int = 40 << 30, n_slots: in
         res = srv.poll()
         for r in res:
             k = id_to_idx.pop(int(r["request"]))
+            if int(r["status"]) == M.MPPI_ERR_NOT_ADMITTED:
+                refused += 1
+                continue
             lat[k] = (r["t_done"] - t_start) - sched.t[k]
             seen[k] = True
             steps_done += float(r["K"]) * float(r["N"])
@@ -103,14 +125,15 @@ def run_served(fleet, sched: Schedule, budget_bytes: int = 40 << 30, n_slots: in
     st = srv.stats()
     srv.close()
     out = _stats(lat[seen], int(seen.sum()), wall, steps_done)
-    out.update({"offered": n, "offered_per_s": n / max(sched.t[-1], 1e-9), "batches": st["batches"],
-                "scratch_peak_gb": st["scratch_peak"] / 1e9, "mean_batch": st["finished"] / max(st["batches"], 1)})
-    return out
+    out.update({"batches": st["batches"], "scratch_peak_gb": st["scratch_peak"] / 1e9,
+                "mean_batch": st["finished"] / max(st["batches"], 1)})
+    return _load(out, n, refused, max(float(sched.t[-1]), 1e-9))
 
 
 def run_plain(fleet, sched: Schedule, K_cap: int = 16384, N_cap: int = 80, dt: float = 0.02,
-              time_limit_s: Optional[float] = None) -> dict:
-    """The same schedule, one mppi_solve per request in arrival order."""
+              time_limit_s: Optional[float] = None, deadline_periods: Optional[float] = None) -> dict:
+    """The same schedule, one mppi_solve per request in arrival order (a
+    request past its deadline when its turn comes is refused)."""
     ctl = []
     for d in fleet:
         sc = W.SolveConfig(objective=d.objective, K=1024, N=30, dt=dt, drone_id=d.drone_id)
@@ -122,13 +145,20 @@ def run_plain(fleet, sched: Schedule, K_cap: int = 16384, N_cap: int = 80, dt: f
     steps = 0.0
     t_start = M.mppi_clock()
     done = 0
+    refused = 0
+    last = n
     for k in range(n):
         now = M.mppi_clock() - t_start
         if time_limit_s is not None and now > time_limit_s:
+            last = k
             break
         if now < sched.t[k]:
             while M.mppi_clock() - t_start < sched.t[k]:
                 pass
+        elif deadline_periods is not None and now > sched.t[k] + deadline_periods * sched.period[k]:
+            refused += 1
+            lat[k] = -1.0
+            continue
         d = int(sched.drone[k])
         if shape[d] != (int(sched.K[k]), int(sched.N[k])):
             ctl[d].set_shape(int(sched.K[k]), int(sched.N[k]))
@@ -140,6 +170,7 @@ def run_plain(fleet, sched: Schedule, K_cap: int = 16384, N_cap: int = 80, dt: f
     wall = M.mppi_clock() - t_start
     for c in ctl:
         c.close()
-    out = _stats(lat[:done], done, wall, steps)
-    out.update({"offered": n, "offered_per_s": n / max(sched.t[-1], 1e-9)})
-    return out
+    served = lat[:last]
+    out = _stats(served[served >= 0], done, wall, steps)
+    # requests the time limit left unstarted count as refused too
+    return _load(out, n, refused + (n - last), max(float(sched.t[-1]), 1e-9))
