@@ -552,8 +552,10 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   __shared__ __align__(8) uint64_t mbar, mbar_never;
   __shared__ double red[32];
   __shared__ float x0s[kNX];
-  __shared__ float4 sBnd[5];  // (sigma, u_min, u_max, 0) per input; (w_limit, omega_max, z_floor, 0)
-  __shared__ int s_adv, s_last, s_group_last, s_bad;
+  // (sigma, u_min, u_max, 0) per input; (w_limit, omega_max, z_floor, 0);
+  // (q_near, r_near^2, 0, 0)
+  __shared__ float4 sBnd[6];
+  __shared__ int s_adv, s_last, s_group_last, s_bad, s_gate0, s_slot0;
   __shared__ double s_theta0, s_m, s_S;
   __shared__ float s_vth0, s_f0, s_qe0, s_rf0;
   __shared__ float2 s_rr;
@@ -575,6 +577,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   if (tid == 0) s_qe0 = quat_norm_excess(x0s[6], x0s[7], x0s[8], x0s[9]);
   if (tid < 4) sBnd[tid] = make_float4(d.sigma[tid], d.u_min[tid], d.u_max[tid], 0.f);
   if (tid == 4) sBnd[4] = make_float4(d.w_limit, d.omega_max, d.z_floor, 0.f);
+  if (tid == 5) sBnd[5] = make_float4(d.q_near, d.r_near2, 0.f, 0.f);
   const int K = d.K, N = d.N, nu = d.nu, B = d.block;
   const int path_smem = path_fits_smem(d.S);
   // the tile: TS = B spt samples; thread tid runs m0 + tid + rep B, rep < spt
@@ -634,6 +637,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
           adv = 1;
       }
       s_adv = adv;
+      s_gate0 = st->gate + adv;
+      s_slot0 = gate_slot(st->gate + adv, d.n_gates, d.closed);
     }
     __syncthreads();
     for (int k = tid; k < N; k += blockDim.x) sPrev[k] = max(0, d.prevcnt[k] - s_adv);
@@ -778,16 +783,15 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       }
       float dT2 = 0.f;
       // objective state
-      // gate progress state: target gate, p_k - g for it (ra), its plane distance
-      int gi = 0, gate_start = 0, slot0 = 0;
+      // gate progress state: p_k - g for the target gate (ra), its plane
+      // distance; the target is gate (s_gate0 + passed), where s_gate0, the
+      // solve's current gate, and its table row s_slot0 are the block's
+      // (shared memory, not registers)
       // the target gate's frame, read from shared memory where it is used
       const GateF* gp = sG;
       float sa = 0.f, rax = 0.f, ray = 0.f, raz = 0.f;
-      const float q_near = d.q_near, r_near2 = d.r_near2;
       if (OBJ == MPPI_OBJ_GATE) {
-        gi = gate_start = st->gate + s_adv;
-        slot0 = gate_slot(gi, d.n_gates, d.closed);
-        gp = sG + slot0;
+        gp = sG + s_slot0;
         rax = s.px - gp->cx;
         ray = s.py - gp->cy;
         raz = s.pz - gp->cz;
@@ -866,14 +870,15 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         if (OBJ == MPPI_OBJ_GATE) {
           // Eq. 7 near-gate term on p_k and the solve's current gate g0
           float ex = rax, ey = ray, ez = raz;
-          if (gi != gate_start) {
-            const GateF& G0 = sG[slot0];
+          if (passed) {
+            const GateF& G0 = sG[s_slot0];
             ex = (s.px - G0.cx) - s.cpx;
             ey = (s.py - G0.cy) - s.cpy;
             ez = (s.pz - G0.cz) - s.cpz;
           }
           const float d0 = ex * ex + ey * ey + ez * ez;
-          near = d0 < r_near2 ? q_near * d0 : 0.f;
+          const float4 nr = lds4_volatile(sBnd + 5);  // (q_near, r_near^2): read here, not held
+          near = d0 < nr.y ? nr.x * d0 : 0.f;
         }
         float dpx, dpy, dpz;
         if (ROT) {
@@ -894,7 +899,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
           stage = dpx * (rax + rbx) + dpy * (ray + rby) + dpz * (raz + rbz) + near;
           float sb = gp->nx * rbx + gp->ny * rby;
           if (sa < 0.f && sb >= 0.f) {
-            const bool open_track_done = (d.closed == 0) && gi >= d.n_gates;
+            const bool open_track_done = (d.closed == 0) && s_gate0 + passed >= d.n_gates;
             const bool ok_time = d.temporal_rule == MPPI_RULE_OFF || sPrev[k] <= passed;
             // crossing point on the segment, relative to the gate centre
             const float a = sa / (sa - sb);
@@ -902,9 +907,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
             const bool open = fabsf(-gp->ny * ex + gp->nx * ey) <= gp->hw && fabsf(ez) <= gp->hh;
             if (!open_track_done && ok_time && open) {
               ++passed;
-              ++gi;
               if (first < 0) first = k;
-              gp = sG + gate_slot(gi, d.n_gates, d.closed);
+              gp = sG + gate_slot(s_gate0 + passed, d.n_gates, d.closed);
               rbx = (s.px - gp->cx) - s.cpx;
               rby = (s.py - gp->cy) - s.cpy;
               rbz = (s.pz - gp->cz) - s.cpz;
