@@ -42,6 +42,9 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+// bytes allocated past the reference table: a bulk copy of its rows is
+// rounded up to 16 bytes
+constexpr int kRefPad = 64;
 
 struct Slab {
   size_t off = 0;
@@ -225,8 +228,9 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   if (p->noise_gen == MPPI_NOISEGEN_SMEM) {
     const int tile = blk * (p->samples_per_thread ? p->samples_per_thread : 1);
     const int Nc = p->N_cap ? p->N_cap : p->N, Kc = p->K_cap ? p->K_cap : p->K;
+    const int rows = p->objective == MPPI_OBJ_TRACK ? ref_rows_for(Nc, p->dt, t->dt_ref, t->T) : 0;
     const uint32_t need = rollout_smem_bytes(Nc, p->objective, t->S, tile, std::max(32, (Kc + tile - 1) / tile),
-                                             MPPI_NOISEGEN_SMEM);
+                                             MPPI_NOISEGEN_SMEM, rows);
     if (need > kRolloutSmemMax)
       return fail(MPPI_ERR_ARG, "noise kept in shared memory needs %u bytes per block, more than %u", need,
                   kRolloutSmemMax);
@@ -242,7 +246,7 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
 }
 
 struct Sizes {
-  size_t off_desc, off_st, off_U, off_prev, off_gates, off_path, off_ref, off_Z, off_Z5, off_J, off_info, off_pm,
+  size_t off_desc, off_st, off_U, off_prev, off_gates, off_gframes, off_path, off_ref, off_Z, off_Z5, off_J, off_info, off_pm,
       off_pS, off_pP, off_ticket, off_unew, off_passcnt, off_xref, total;
 };
 
@@ -264,8 +268,9 @@ Sizes plan_sizes(const mppi_params_t* p, const mppi_track_t* t) {
   z.off_U = s.take(sizeof(float) * (N_cap * kNU + 8));
   z.off_prev = s.take(sizeof(int32_t) * (N_cap + 8));
   z.off_gates = s.take(sizeof(float) * 6 * std::max(1, t->n_gates));
+  z.off_gframes = s.take(sizeof(GateF) * std::max(1, t->n_gates));
   z.off_path = s.take(sizeof(float) * 6 * std::max(1, t->S) + 64);
-  z.off_ref = s.take(sizeof(float) * 13 * std::max(1, t->T));
+  z.off_ref = s.take(sizeof(float) * 13 * std::max(1, t->T) + kRefPad);
   z.off_Z = s.take(stored ? (size_t)N_cap * K_cap * (bf16 ? 8 : 16) : 16);
   z.off_Z5 = s.take(five && stored ? (size_t)N_cap * K_cap * (bf16 ? 2 : 4) : 16);
   z.off_J = s.take(sizeof(double) * K_cap);
@@ -544,6 +549,9 @@ int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mp
   d.ref = reinterpret_cast<float*>(b + z.off_ref);
   d.T = track->T;
   d.dt_ref = track->dt_ref;
+  d.gframes = reinterpret_cast<const GateF*>(b + z.off_gframes);
+  d.ref_rows = d.objective == MPPI_OBJ_TRACK ? ref_rows_for(h->N_cap, d.dt, d.dt_ref, d.T) : 0;
+  d.ref_pad = kRefPad;
   const bool bf16 = d.noise_bf16,
              stored = d.noise_gen != MPPI_NOISEGEN_REGEN && d.noise_gen != MPPI_NOISEGEN_SMEM;
   d.Z4 = (stored && !bf16) ? reinterpret_cast<float4*>(b + z.off_Z) : nullptr;
@@ -568,6 +576,10 @@ int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mp
   if (track->n_gates > 0 && track->gates &&
       cudaMemcpy((void*)d.gates, track->gates, sizeof(float) * 6 * track->n_gates, cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "upload of gates failed"));
+  if (track->n_gates > 0 && track->gates &&
+      (launch_gate_frames(d.gates, track->n_gates, const_cast<GateF*>(d.gframes), 0) != cudaSuccess ||
+       cudaStreamSynchronize(0) != cudaSuccess))
+    return cleanup(fail(MPPI_ERR_CUDA, "gate frames failed"));
   if (track->S > 0 && track->path &&
       cudaMemcpy((void*)d.path, track->path, sizeof(float) * 6 * track->S, cudaMemcpyHostToDevice))
     return cleanup(fail(MPPI_ERR_CUDA, "upload of path failed"));
@@ -659,7 +671,8 @@ static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   } else {
     CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
   }
-  const uint32_t smem = rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles), gen);
+  const uint32_t smem =
+      rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles), gen, d.ref_rows);
   CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen,
                     d.rotor));
   return MPPI_OK;
@@ -728,7 +741,13 @@ int mppi_get_unew(mppi_handle h, float* U) {
 }
 int mppi_get_costs(mppi_handle h, double* J) {
   if (!h || !J) return fail(MPPI_ERR_ARG, "null argument");
+  // the device keeps each cost as its compensated (hi, lo) binary32 pair
   CU(cudaMemcpy(J, h->hd.J, sizeof(double) * h->hd.K, cudaMemcpyDeviceToHost));
+  for (int m = 0; m < h->hd.K; ++m) {
+    float pair[2];
+    memcpy(pair, &J[m], sizeof pair);
+    J[m] = (double)pair[0] + (double)pair[1];
+  }
   return MPPI_OK;
 }
 int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass) {
@@ -1088,7 +1107,7 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
     rsmem[gi] =
         std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles),
-                                               d.noise_gen));
+                                               d.noise_gen, d.ref_rows));
     const int gn = d.noise_gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
       rg[gi].second.push_back(Tile{i, t * tile_samples(d)});

@@ -55,6 +55,13 @@ struct StepConsts {
   float4 c[2];
 };
 
+// gate frame: centre, plane normal (horizontal), half sizes; a handle keeps
+// one per gate in device memory, and the rollout stages them in shared
+// memory by a bulk copy (32 bytes each, read as two float4)
+struct __align__(16) GateF {
+  float cx, cy, cz, nx, ny, hw, hh, pad;
+};
+
 // --------------------------------------------------------------------------
 // per-handle solve descriptor (device memory, read by every block)
 // --------------------------------------------------------------------------
@@ -80,14 +87,17 @@ struct SolveDesc {
   float Q[kNX], QN[kNX], R[4];
   float hover;
   // track (device pointers)
-  const float* gates;   // [n][6]
+  const float* gates;   // [n][6] centre, yaw, half width, half height
+  const GateF* gframes; // [n] the frames of those gates (built once per handle)
   int32_t n_gates, closed;
   const float* path;    // [S][6]
   int32_t S;
   float L, ds, inv_ds;
-  const float* ref;     // [T][13]
+  const float* ref;     // [T][13] (16-byte aligned)
   int32_t T;
   float dt_ref;
+  int32_t ref_rows;     // reference rows a tracking block stages in shared memory (0: reads them from ref)
+  int32_t ref_pad;      // bytes readable past the end of ref (a bulk copy is rounded up to 16 bytes)
   // resident state
   DevState* st;
   float* U;             // [N_cap][5] (+pad), always fully populated
@@ -98,7 +108,7 @@ struct SolveDesc {
   uint2* Zb;            // [N][K] 4 x bf16 (BF16 storage)
   float* Z5;            // [N][K] 5th normal (contouring, F32)
   __nv_bfloat16* Z5b;   // [N][K] 5th normal (contouring, BF16)
-  double* J;            // [K]
+  double* J;            // [K] cost as a (hi, lo) float pair per 8-byte slot: J = hi + lo
   int32_t* info;        // [K] npass | (first_pass + 1) << 16
   double* part_m;       // [tiles] per-tile minimum cost
   double* part_S;       // [tiles] per-tile sum of exp weights
@@ -612,10 +622,5 @@ __device__ __forceinline__ float limit_penalty(float wlim, float wmax, float zf,
   return wlim * (ex * ex + ey * ey + ez * ez + e * e);
 }
 
-// gate frame in shared memory: centre, plane normal (horizontal), half sizes
-// (16-byte aligned: read as two float4)
-struct __align__(16) GateF {
-  float cx, cy, cz, nx, ny, hw, hh, pad;
-};
 
 }  // namespace mppi

@@ -14,8 +14,30 @@
 
 namespace mppi {
 
-uint32_t rollout_smem_bytes(int N, int objective, int S, int tile, int merge_cap, int gen) {
-  return smem_layout(N, objective, S, tile, merge_cap, path_fits_smem(S), gen).total;
+static std::atomic<unsigned long long> g_launches{0};  // host threads may launch concurrently
+unsigned long long launches_so_far() { return g_launches.load(); }
+void add_launches(int n) { g_launches += (unsigned long long)n; }
+
+uint32_t rollout_smem_bytes(int N, int objective, int S, int tile, int merge_cap, int gen, int ref_rows) {
+  return smem_layout(N, objective, S, tile, merge_cap, path_fits_smem(S), gen, ref_rows).total;
+}
+
+// the frame of every gate (centre, plane normal from the yaw, half sizes)
+__global__ void gate_frames_kernel(const float* __restrict__ raw, int n, GateF* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* g = raw + 6 * i;
+  float s, c;
+  sincosf(g[3], &s, &c);
+  out[i] = GateF{g[0], g[1], g[2], c, s, g[4], g[5], 0.f};
+}
+
+cudaError_t launch_gate_frames(const float* raw, int n, GateF* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  (void)cudaGetLastError();
+  gate_frames_kernel<<<(n + 63) / 64, 64, 0, s>>>(raw, n, out);
+  ++g_launches;
+  return cudaGetLastError();
 }
 
 int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; }
@@ -95,12 +117,7 @@ __global__ void __launch_bounds__(128) nominal_kernel(const SolveDesc* __restric
   const int adv = st->adv;
   for (int k = lane; k < N; k += 32) sPrev[w][k] = max(0, d.prevcnt[k] - adv);
   if (lane < 2) sSC[w].c[lane] = d.stepc.c[lane];
-  for (int g = lane; g < d.n_gates; g += 32) {
-    const float* gr = d.gates + 6 * g;
-    float s, c;
-    sincosf(gr[3], &s, &c);
-    sG[w][g] = GateF{gr[0], gr[1], gr[2], c, s, gr[4], gr[5], 0.f};
-  }
+  for (int g = lane; g < d.n_gates; g += 32) sG[w][g] = d.gframes[g];
   __syncwarp();
   int pc_last = 0;
   if (lane == 0) {
@@ -229,9 +246,6 @@ __global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, StepConsts SC, i
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-static std::atomic<unsigned long long> g_launches{0};  // host threads may launch concurrently
-unsigned long long launches_so_far() { return g_launches.load(); }
-void add_launches(int n) { g_launches += (unsigned long long)n; }
 
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
                          cudaStream_t s, int nominal) {

@@ -21,7 +21,16 @@ __host__ __device__ inline int n_groups_for(int T) {
 
 __host__ __device__ int path_fits_smem(int S);
 // dynamic shared memory of a rollout launch (gen: MPPI_NOISEGEN_*)
-uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap, int gen);
+uint32_t rollout_smem_bytes(int N, int objective, int S, int block, int merge_cap, int gen, int ref_rows);
+// reference rows a tracking block stages in shared memory for a horizon of
+// N_cap steps (0: the window reads the table in global memory)
+inline int ref_rows_for(int N_cap, float dt, float dt_ref, int T) {
+  if (!(dt_ref > 0.f) || T < 2) return 0;
+  const double rows = (double)N_cap * (double)dt / (double)dt_ref + 4.0;
+  return rows * 52.0 <= 48.0 * 1024.0 && rows <= (double)T ? (int)rows : 0;
+}
+// frames of n gates from the [n][6] table (device pointers)
+cudaError_t launch_gate_frames(const float* raw, int n, GateF* out, cudaStream_t s);
 // largest dynamic shared memory a rollout launch may use
 constexpr uint32_t kRolloutSmemMax = 200 * 1024;
 unsigned long long launches_so_far();

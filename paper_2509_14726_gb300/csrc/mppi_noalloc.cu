@@ -12,6 +12,7 @@
 // of fixed size that is loaded with the library.
 #include <cstdio>
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -58,7 +59,7 @@ int scratch_on_device(int dev, void** out) {
 }
 
 struct Layout {
-  size_t desc, st, tiles, U, prev, Z, Z5, J, info, pm, pS, pP, ticket, passcnt, xref, total;
+  size_t desc, st, tiles, U, prev, gframes, Z, Z5, J, info, pm, pS, pP, ticket, passcnt, xref, total;
 };
 
 Layout layout_for(int K, int N, int block, int five, int bf16, bool stored) {
@@ -78,6 +79,7 @@ Layout layout_for(int K, int N, int block, int five, int bf16, bool stored) {
   L.tiles = take(sizeof(Tile) * T);
   L.U = take(sizeof(float) * (N * kNU + 8));
   L.prev = take(sizeof(int32_t) * (N + 8));
+  L.gframes = take(sizeof(GateF) * MPPI_MAX_GATES);
   L.Z = take(stored ? (size_t)N * K * (bf16 ? 8 : 16) : 16);
   L.Z5 = take(five && stored ? (size_t)N * K * (bf16 ? 2 : 4) : 16);
   L.J = take(sizeof(double) * K);
@@ -144,8 +146,9 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (d_track->n_gates < 0 || d_track->n_gates > MPPI_MAX_GATES) return fail(MPPI_ERR_ARG, "n_gates out of range");
   if (p.noise_gen == MPPI_NOISEGEN_SMEM) {
     const int tile = block * (p.samples_per_thread ? p.samples_per_thread : 1);
+    const int rows = p.objective == MPPI_OBJ_TRACK ? ref_rows_for(p.N, p.dt, d_track->dt_ref, d_track->T) : 0;
     if (rollout_smem_bytes(p.N, p.objective, d_track->S, tile, std::max(32, (p.K + tile - 1) / tile),
-                           MPPI_NOISEGEN_SMEM) > kRolloutSmemMax)
+                           MPPI_NOISEGEN_SMEM, rows) > kRolloutSmemMax)
       return fail(MPPI_ERR_ARG, "noise kept in shared memory does not fit a block's shared memory");
   }
   if (gate < 0) return fail(MPPI_ERR_ARG, "gate index is negative");
@@ -180,6 +183,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   memset(&d, 0, sizeof d);
   fill_model_params(m, p, five ? 5 : 4, d);
   d.gates = d_track->gates;
+  d.gframes = reinterpret_cast<const GateF*>(b + L.gframes);
   d.n_gates = d_track->n_gates;
   d.closed = d_track->closed ? 1 : 0;
   d.path = d_track->path;
@@ -190,6 +194,12 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   d.ref = d_track->ref;
   d.T = d_track->T;
   d.dt_ref = d_track->dt_ref;
+  // the caller's reference table: staged by bulk copies only from a 16-byte
+  // aligned table, and never past its end (no padding is known)
+  d.ref_rows = p.objective == MPPI_OBJ_TRACK && d_track->ref && reinterpret_cast<uintptr_t>(d_track->ref) % 16 == 0
+                   ? ref_rows_for(p.N, p.dt, d_track->dt_ref, d_track->T)
+                   : 0;
+  d.ref_pad = 0;
   d.st = reinterpret_cast<DevState*>(b + L.st);
   d.U = reinterpret_cast<float*>(b + L.U);
   d.prevcnt = reinterpret_cast<int32_t*>(b + L.prev);
@@ -221,6 +231,9 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   noalloc_tiles_kernel<<<(d.n_tiles + 255) / 256, 256, 0, s>>>(d_tiles, d.n_tiles, tile_samples(d));
   add_launches(2);
   if (cudaGetLastError() != cudaSuccess) return fail(MPPI_ERR_CUDA, "set-up kernel launch failed");
+  if (p.objective == MPPI_OBJ_GATE &&
+      launch_gate_frames(d_track->gates, d_track->n_gates, const_cast<GateF*>(d.gframes), s) != cudaSuccess)
+    return fail(MPPI_ERR_CUDA, "gate frame launch failed");
   if (d.noise_gen == MPPI_NOISEGEN_KERNEL &&
       launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s, d.nominal_sample) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "noise kernel launch failed");
@@ -232,7 +245,8 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   io.u0 = d_u0;
   io.status = nullptr;
   const uint32_t smem =
-      rollout_smem_bytes(p.N, p.objective, d.S, tile_samples(d), d.n_tiles > 32 ? d.n_tiles : 32, p.noise_gen);
+      rollout_smem_bytes(p.N, p.objective, d.S, tile_samples(d), d.n_tiles > 32 ? d.n_tiles : 32, p.noise_gen,
+                         d.ref_rows);
   if (launch_rollout(p.objective, bf16, d_desc, d_tiles, d.n_tiles, block, smem, io, s, d.noise_gen, d.rotor) !=
       cudaSuccess)
     return fail(MPPI_ERR_CUDA, "rollout kernel launch failed");

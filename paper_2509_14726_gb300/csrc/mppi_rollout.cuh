@@ -199,15 +199,16 @@ __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
 // shared-memory layout of the rollout kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_e, off_j, off_merge, off_z, total;
+  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_ref, off_e, off_j, off_merge, off_z, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // tile: samples per tile (threads per block x samples per thread); gen: where
 // the normals are drawn (MPPI_NOISEGEN_SMEM keeps the tile's normals here)
+// ref_rows: reference rows a tracking block stages (0: none)
 __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, int tile, int merge_cap,
-                                                  int path_in_smem, int gen) {
+                                                  int path_in_smem, int gen, int ref_rows) {
   SmemLayout L;
   uint32_t o = 0;
   L.off_U = o;
@@ -220,6 +221,8 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
   if (objective == MPPI_OBJ_CONTOUR && path_in_smem) o += align16((uint32_t)S * 6u * 4u);
   L.off_xref = o;
   if (objective == MPPI_OBJ_TRACK) o += align16((uint32_t)(N + 1) * kNX * 4u) + align16((uint32_t)(N + 1) * 16u);
+  L.off_ref = o;  // staged reference rows: two segments, each from a 16-byte boundary
+  if (objective == MPPI_OBJ_TRACK && ref_rows > 0) o += align16((uint32_t)ref_rows * 52u + 16u) + 16u;
   L.off_e = o;
   o += align16((uint32_t)tile * 4u);
   L.off_j = o;  // the tile's costs as compensated pairs: [tile] hi, then [tile] lo
@@ -559,7 +562,11 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   __shared__ double s_theta0, s_m, s_S;
   __shared__ float s_vth0, s_f0, s_qe0, s_rf0;
   __shared__ float2 s_rr;
-  __shared__ int s_j0, s_ri0;
+  __shared__ int s_j0, s_ri0, s_win[2];
+  // staged reference rows: rows before the wrap, first row's byte offset in
+  // its 16-byte-aligned copy, offset of the second copy, copy sizes, source
+  __shared__ int s_ref_n1, s_ref_lead, s_ref_seg2;
+  __shared__ uint32_t s_ref_len[2], s_ref_src;
   __shared__ float s_best_d[32];
   __shared__ int s_best_j[32];
   __shared__ float s_best_t[32];
@@ -582,7 +589,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   const int path_smem = path_fits_smem(d.S);
   // the tile: TS = B spt samples; thread tid runs m0 + tid + rep B, rep < spt
   const int spt = d.spt, TS = B * spt;
-  const SmemLayout Ls = smem_layout(N, OBJ, d.S, TS, max(d.n_tiles, 32), path_smem, GEN);
+  const SmemLayout Ls = smem_layout(N, OBJ, d.S, TS, max(d.n_tiles, 32), path_smem, GEN, d.ref_rows);
   // GEN 3: the tile's normals, kept here for the update (Eq. 5)
   float4* sZ4 = reinterpret_cast<float4*>(smem + Ls.off_z);
   float* sZ5 = reinterpret_cast<float*>(smem + Ls.off_z + align16((uint32_t)N * TS * 16u));
@@ -597,34 +604,82 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   double* sMerge = reinterpret_cast<double*>(smem + Ls.off_merge);
   const float* path = path_smem ? sPath : d.path;
 
-  // ---- prologue: TMA bulk copies of the nominal and the path table ----
+  // ---- prologue: TMA bulk copies into shared memory of the nominal, the
+  // gate frames (gate progress), the path table (contouring) and the span of
+  // reference rows the tracking window reads ----
   const uint32_t bytes_U = align16((uint32_t)N * kNU * 4u);
   const uint32_t bytes_path = (OBJ == MPPI_OBJ_CONTOUR && path_smem) ? align16((uint32_t)d.S * 24u) : 0u;
+  const uint32_t bytes_gates = OBJ == MPPI_OBJ_GATE ? (uint32_t)d.n_gates * (uint32_t)sizeof(GateF) : 0u;
+  unsigned char* sRef = smem + Ls.off_ref;
+  DevState* st = d.st;
   if (tid == 0) {
     mbar_init(&mbar, 1);
     if (d.wait_unreachable) mbar_init(&mbar_never, 1);
     s_bad = 0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    mbar_expect_tx(&mbar, bytes_U + bytes_path);
+    uint32_t bytes_ref = 0;
+    if (OBJ == MPPI_OBJ_TRACK) {
+      // the time origin as a table position (row i0, fraction f0), once per
+      // block; the step positions f0 + k dt/dt_ref are formed below in
+      // binary32 with dt/dt_ref as a (hi, lo) pair
+      const double t0 = io.t0 ? io.t0[tile.solve] : io.t0v;
+      const double period = (double)d.T * (double)d.dt_ref;
+      double tau = fmod(t0, period);
+      if (tau < 0) tau += period;
+      const double s0 = tau / (double)d.dt_ref;
+      const double fi = floor(s0);
+      int i0 = (int)fi;  // tau rounds up to the period at most: row T is row 0
+      if (i0 >= d.T) i0 -= d.T;
+      s_ri0 = i0;
+      s_rf0 = (float)(s0 - fi);
+      const float r = d.dt / d.dt_ref;
+      s_rr = make_float2(r, fmaf(-r, d.dt_ref, d.dt) / d.dt_ref);
+      // rows i0 .. i0 + n - 1 (mod T) hold every step's pair of rows; staged
+      // as up to two bulk copies (the second after the wrap to row 0), each
+      // from a 16-byte boundary at or below its first row
+      const int n = (int)floor((double)s_rf0 + (double)N * ((double)d.dt / (double)d.dt_ref)) + 3;
+      s_ref_n1 = 0;
+      if (d.ref_rows > 0 && n <= d.ref_rows && n <= d.T) {
+        const int n1 = min(n, d.T - i0), n2 = n - n1;
+        const uint32_t b0 = 52u * (uint32_t)i0, a0 = b0 & ~15u, len1 = align16(b0 - a0 + 52u * (uint32_t)n1);
+        const uint32_t len2 = n2 > 0 ? align16(52u * (uint32_t)n2) : 0u;
+        const uint32_t table = 52u * (uint32_t)d.T + (uint32_t)d.ref_pad;
+        if (a0 + len1 <= table && len2 <= table && len1 + 16u + len2 <= align16((uint32_t)d.ref_rows * 52u + 16u) + 16u) {
+          s_ref_n1 = n1;
+          s_ref_lead = (int)(b0 - a0);
+          s_ref_seg2 = (int)align16(len1);
+          bytes_ref = len1 + len2;
+          s_ref_len[0] = len1;
+          s_ref_len[1] = len2;
+          s_ref_src = a0;
+        }
+      }
+    }
+    mbar_expect_tx(&mbar, bytes_U + bytes_path + bytes_gates + bytes_ref);
     bulk_g2s(sU, d.U, bytes_U, &mbar);
     if (bytes_path) bulk_g2s(sPath, d.path, bytes_path, &mbar);
+    if (bytes_gates) bulk_g2s(sG, d.gframes, bytes_gates, &mbar);
+    if (bytes_ref) {
+      bulk_g2s(sRef, reinterpret_cast<const unsigned char*>(d.ref) + s_ref_src, s_ref_len[0], &mbar);
+      if (s_ref_len[1]) bulk_g2s(sRef + s_ref_seg2, d.ref, s_ref_len[1], &mbar);
+    }
   }
-  DevState* st = d.st;
   // GEN != 0: the normals are drawn here (GEN 1 stores them in global memory,
   // GEN 2 draws them again in the epilogue, GEN 3 keeps them in shared
   // memory) instead of being loaded from the noise kernel's output
   const uint32_t iter = GEN ? st->iter : 0u;
-  // gate frames (computed here from the raw table: centre, yaw, half sizes)
+  // ---- wait for the bulk copies (bounded) ----
+  // A wait that gives up marks the block's samples invalid and counts a
+  // timeout, which the solve reports as MPPI_ERR_TIMEOUT; a second bounded
+  // wait then lets the copies land before the block uses or releases the
+  // shared memory they write.  (For testing, the first wait can target a
+  // barrier that no copy ever completes.)
+  __syncthreads();
+  if (!mbar_wait(d.wait_unreachable ? &mbar_never : &mbar, 0, d.wait_ns)) {
+    if (tid == 0) { s_bad = 1; atomicAdd(&st->timeouts, 1); }
+    mbar_wait(&mbar, 0, 200000000ull);
+  }
+  __syncthreads();
   if (OBJ == MPPI_OBJ_GATE) {
-    for (int i = tid; i < d.n_gates; i += blockDim.x) {
-      const float* g = d.gates + 6 * i;
-      float s, c;
-      sincosf(g[3], &s, &c);
-      sG[i] = GateF{g[0], g[1], g[2], c, s, g[4], g[5], 0.f};
-    }
-    __syncthreads();
     if (tid == 0) {
       // the plant's own pass of the current gate since the last solve
       int adv = 0;
@@ -645,23 +700,15 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   }
   if (OBJ == MPPI_OBJ_TRACK) {
     // reference window x_ref(t0 + k dt), k = 0..N: linear in the table, nlerp
-    // for q.  The time origin becomes a table position (row i0, fraction f0)
-    // once per block; the step positions f0 + k dt/dt_ref are then formed in
-    // binary32 with dt/dt_ref as a (hi, lo) pair and exact integer parts.
-    if (tid == 0) {
-      const double t0 = io.t0 ? io.t0[tile.solve] : io.t0v;
-      const double period = (double)d.T * (double)d.dt_ref;
-      double tau = fmod(t0, period);
-      if (tau < 0) tau += period;
-      const double s0 = tau / (double)d.dt_ref;
-      const double fi = floor(s0);
-      s_ri0 = (int)fi;
-      s_rf0 = (float)(s0 - fi);
-      const float r = d.dt / d.dt_ref;
-      s_rr = make_float2(r, fmaf(-r, d.dt_ref, d.dt) / d.dt_ref);
-    }
-    __syncthreads();
+    // for q, from the staged rows (or the table, where they were not staged)
     const float2 rr = s_rr;
+    const int n1 = s_ref_n1;
+    auto row = [&](int i) -> const float* {
+      if (!n1) return d.ref + (size_t)13 * i;
+      int q = i - s_ri0;
+      if (q < 0) q += d.T;
+      return reinterpret_cast<const float*>(q < n1 ? sRef + s_ref_lead + 52 * q : sRef + s_ref_seg2 + 52 * (q - n1));
+    };
     for (int k = tid; k <= N; k += blockDim.x) {
       const float kf = (float)k;
       const float p = kf * rr.x;
@@ -673,8 +720,8 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       int i = (s_ri0 + (int)ip + (int)fl) % d.T;
       if (i < 0) i += d.T;
       const int i1 = i + 1 < d.T ? i + 1 : 0;
-      const float* a = d.ref + (size_t)13 * i;
-      const float* b = d.ref + (size_t)13 * i1;
+      const float* a = row(i);
+      const float* b = row(i1);
       float* o = sX + (size_t)13 * k;
       float* ol = sXl + (size_t)4 * k;
       for (int c = 0; c < 13; ++c) o[c] = fmaf(f, b[c] - a[c], a[c]);
@@ -692,27 +739,25 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       const float rn = 1.0f / sqrtf(n2);
       for (int c = 6; c < 10; ++c) o[c] *= rn;
     }
+    __syncthreads();
   }
-  // ---- wait for the bulk copies (bounded) ----
-  // A wait that gives up marks the block's samples invalid and counts a
-  // timeout, which the solve reports as MPPI_ERR_TIMEOUT; a second bounded
-  // wait then lets the copies land before the block uses or releases the
-  // shared memory they write.  (For testing, the first wait can target a
-  // barrier that no copy ever completes.)
-  if (!mbar_wait(d.wait_unreachable ? &mbar_never : &mbar, 0, d.wait_ns)) {
-    if (tid == 0) { s_bad = 1; atomicAdd(&st->timeouts, 1); }
-    mbar_wait(&mbar, 0, 200000000ull);
-  }
-  __syncthreads();
   if (OBJ == MPPI_OBJ_CONTOUR) {
     // theta_0: closest point of the path to x0 among the node segments of the
-    // window [theta_prev - back, theta_prev + ahead] (whole path on the first solve)
-    const double dsd = (double)d.L / (double)d.S;
-    int jlo = 0, jhi = d.S - 1;
-    if (st->has_theta) {
-      jlo = (int)floor((st->theta - (double)d.theta_back) / dsd);
-      jhi = (int)floor((st->theta + (double)d.theta_ahead) / dsd);
+    // window [theta_prev - back, theta_prev + ahead] (whole path on the first
+    // solve).  The window's node indices come from the FP64 progress state,
+    // once per block (one thread; the search itself is binary32).
+    if (tid == 0) {
+      int jlo = 0, jhi = d.S - 1;
+      if (st->has_theta) {
+        const double dsd = (double)d.L / (double)d.S;
+        jlo = (int)floor((st->theta - (double)d.theta_back) / dsd);
+        jhi = (int)floor((st->theta + (double)d.theta_ahead) / dsd);
+      }
+      s_win[0] = jlo;
+      s_win[1] = jhi;
     }
+    __syncthreads();
+    const int jlo = s_win[0], jhi = s_win[1];
     float best = INFINITY, bt = 0.f;
     int bj = 0x7fffffff;
     for (int jj = jlo + tid; jj <= jhi; jj += blockDim.x) {
@@ -747,7 +792,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       if (j < 0) j += d.S;
       s_j0 = j;
       s_f0 = bt * d.ds;  // metres past node j0
-      double th = ((double)j + (double)bt) * dsd;
+      const double th = ((double)j + (double)bt) * ((double)d.L / (double)d.S);
       s_theta0 = th;
       s_vth0 = st->has_theta ? (float)st->v_theta : 0.f;
     }
@@ -984,7 +1029,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
     // per-sample outputs; the cost pair stays in shared memory for Eq. 4
     const bool valid = active && isfinite(Jh) && isfinite(Jc) && isfinite(Jh - Jc);
     if (active) {
-      d.J[m] = (double)Jh - (double)Jc;
+      d.J[m] = pack2(Jh, -Jc);  // the compensated pair itself: no FP64 arithmetic here
       d.info[m] = passed | ((first + 1) << 16);
     }
     if (tid < B) {

@@ -316,8 +316,9 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
     return sfail(MPPI_ERR_ARG, "bad noise generation mode");
   if (p.noise_gen == MPPI_NOISEGEN_SMEM) {
     const int tile = block * (p.samples_per_thread ? p.samples_per_thread : 1);
+    const int rows = p.objective == MPPI_OBJ_TRACK ? ref_rows_for(N_cap, p.dt, track->dt_ref, track->T) : 0;
     if (rollout_smem_bytes(N_cap, p.objective, track->S, tile, std::max(32, (K_cap + tile - 1) / tile),
-                           MPPI_NOISEGEN_SMEM) > kRolloutSmemMax)
+                           MPPI_NOISEGEN_SMEM, rows) > kRolloutSmemMax)
       return sfail(MPPI_ERR_ARG, "noise kept in shared memory does not fit a block's shared memory");
   }
   if (p.samples_per_thread < 0 || p.samples_per_thread > MPPI_MAX_SPT)
@@ -349,8 +350,9 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   };
   const size_t o_st = take(sizeof(DevState)), o_U = take(sizeof(float) * (N_cap * kNU + 8)),
                o_prev = take(sizeof(int32_t) * (N_cap + 8)), o_g = take(sizeof(float) * 6 * std::max(1, track->n_gates)),
+               o_gf = take(sizeof(GateF) * std::max(1, track->n_gates)),
                o_path = take(sizeof(float) * 6 * std::max(1, track->S) + 64),
-               o_ref = take(sizeof(float) * 13 * std::max(1, track->T)), o_unew = take(sizeof(float) * N_cap * kNU),
+               o_ref = take(sizeof(float) * 13 * std::max(1, track->T) + 64), o_unew = take(sizeof(float) * N_cap * kNU),
                o_pc = take(sizeof(int32_t) * (N_cap + 1)), o_xref = take(sizeof(float) * 13 * (N_cap + 1)),
                o_tk = take(sizeof(uint32_t) * (Gn + 2));
   if (cudaMalloc(&d.slab, o) != cudaSuccess) {
@@ -377,13 +379,19 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   h.ref = reinterpret_cast<float*>(b + o_ref);
   h.T = track->T;
   h.dt_ref = track->dt_ref;
+  h.gframes = reinterpret_cast<const GateF*>(b + o_gf);
+  h.ref_rows = p.objective == MPPI_OBJ_TRACK ? ref_rows_for(N_cap, p.dt, track->dt_ref, track->T) : 0;
+  h.ref_pad = 64;
   h.unew = reinterpret_cast<float*>(b + o_unew);
   h.passcnt = reinterpret_cast<int32_t*>(b + o_pc);
   h.xref = reinterpret_cast<float*>(b + o_xref);
   h.ticket = reinterpret_cast<uint32_t*>(b + o_tk);
   h.block = block;
-  if (track->n_gates > 0 && track->gates)
+  if (track->n_gates > 0 && track->gates) {
     SCU(cudaMemcpy((void*)h.gates, track->gates, sizeof(float) * 6 * track->n_gates, cudaMemcpyHostToDevice));
+    SCU(launch_gate_frames(h.gates, track->n_gates, const_cast<GateF*>(h.gframes), 0));
+    SCU(cudaStreamSynchronize(0));
+  }
   if (track->S > 0 && track->path)
     SCU(cudaMemcpy((void*)h.path, track->path, sizeof(float) * 6 * track->S, cudaMemcpyHostToDevice));
   if (track->T > 0 && track->ref)
@@ -580,7 +588,8 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
     }
     for (int t = 0; t < dd.n_tiles; ++t) groups[g].t.push_back(Tile{i, t * tile_samples(dd)});
     groups[g].smem = std::max(groups[g].smem, rollout_smem_bytes(dd.N, dd.objective, dd.S, tile_samples(dd),
-                                                                 dd.n_tiles > 32 ? dd.n_tiles : 32, dd.noise_gen));
+                                                                 dd.n_tiles > 32 ? dd.n_tiles : 32, dd.noise_gen,
+                                                                 dd.ref_rows));
     if (dd.objective == MPPI_OBJ_GATE) which.push_back(i);
   }
   Tile* htiles = reinterpret_cast<Tile*>(sl.host + st.tiles);

@@ -559,3 +559,36 @@ def test_bounded_wait_reports_a_timeout_and_keeps_the_nominal(O, M):
     r = ora.solve(x, 0.0)
     compare(gpu, r, "after a timed-out solve")
     gpu.close()
+
+
+def test_reference_rows_staged_or_read_give_the_same_solve(M):
+    """A tracking block stages the reference rows its window needs in shared
+    memory by bulk copies (two when the window wraps past the end of the
+    table) unless they would not fit, and then reads the table directly.  On
+    a reference ten times finer than usual (dt_ref / 10), a handle of horizon
+    cap 20 stages its rows and one of cap 128 cannot; the same solves,
+    including windows across the wrap, agree bit for bit."""
+    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_TRACK)
+    sc.K, sc.N = 1024, 20
+    fine = 10
+    T = tr.ref.shape[0]
+    ref = np.zeros((T * fine, 13))
+    for j in range(fine):
+        a, b = tr.ref, np.roll(tr.ref, -1, axis=0)
+        f = j / fine
+        ref[j::fine] = (1 - f) * a + f * b
+    ref[:, 6:10] /= np.linalg.norm(ref[:, 6:10], axis=1, keepdims=True)
+    tr = W.Track(tr.gates, tr.closed, tr.path, tr.L, ref, tr.dt_ref / fine)
+    case = f32_case(mc, sc, tr, x0)
+    staged = M.Controller(case.mc, case.sc, case.tr)
+    direct = M.Controller(case.mc, case.sc, case.tr, N_cap=128)
+    period = T * fine * float(np.float32(tr.dt_ref))
+    for t0 in (0.3, period - 0.1, period - 0.01):
+        x = np.float32(tr.ref[int(t0 / tr.dt_ref) % (T * fine)]).astype(np.float64)
+        ua, _ = staged.solve(x, t0)
+        ub, _ = direct.solve(x, t0)
+        np.testing.assert_array_equal(ua, ub)
+        np.testing.assert_array_equal(staged.costs(), direct.costs())
+        np.testing.assert_array_equal(staged.xref(), direct.xref()[: sc.N + 1])
+    staged.close()
+    direct.close()
