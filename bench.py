@@ -526,7 +526,7 @@ def main():
     traffic = measured_traffic(steps_by_obj)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "rollout_kernel (3 launches, one per objective)",
-                "traffic_note": "DRAM bytes of the 3 launches: ncu per-step figures of the 32-drone capture "
+                "traffic_note": "DRAM bytes of the 3 launches: ncu per-step figures of the 64-drone capture "
                                 "scaled by this batch's K x N (null if the kernel source changed since)",
                 "peak_note": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 x 2070 MHz (max SM clock)",
                 "phase_ms": {"noise": float(prof[0]), "rollout_gate": float(prof[1]),
