@@ -106,31 +106,54 @@ def measured_fp32_ops(steps_by_objective):
 
 def paper_table1_latency(M, W, reps: int = 300) -> dict:
     """Single-solve latency at the paper's Table I size for each objective
-    (the paper reports about 0.4 ms on an RTX 3090 for 8192 samples), with the
-    separate noise pass and with the normals kept in shared memory: host-
-    synchronous mppi_solve p50 / p99 and device time per solve back to back
-    (ms)."""
+    (the paper reports about 0.4 ms on an RTX 3090 for 8192 samples), for
+    three ways of drawing the normals: the separate Philox pass before the
+    rollout, the rollout keeping them in shared memory, and the separate pass
+    run after each solve for the next one.  Columns (ms):
+      p50, p99: host-synchronous mppi_solve through the Python binding, the
+                device idle when the call starts (a controller that solves
+                once per control period);
+      c_p50:    the same call made through ctypes with the arguments built
+                once (the C-ABI call itself, without the binding's marshalling);
+      device:   device time per solve, solves enqueued back to back
+                (mppi_solve_async; for the ahead mode this includes the draw
+                for the next solve)."""
+    import ctypes as C
     import torch
     out = {}
     names = {0: "gate", 1: "contour", 2: "track"}
+    modes = (("noise_pass", M.NOISEGEN_KERNEL), ("noise_in_smem", M.NOISEGEN_SMEM),
+             ("noise_ahead", M.NOISEGEN_AHEAD))
+    L = M.load()
     for K in (8192, 2048):
         for obj in (0, 1, 2):
             mc, sc, tr, x0 = W.paper_table1(obj, K)
             if obj == 2:
                 x0 = tr.ref[0].astype(np.float64)  # on the reference at t = 0
             row = {}
-            for mode, gen in (("noise_pass", M.NOISEGEN_KERNEL), ("noise_in_smem", M.NOISEGEN_SMEM)):
+            for mode, gen in modes:
                 ctl = M.Controller(mc, sc, tr, noise_gen=gen)
                 for _ in range(30):
                     ctl.solve(x0, 0.0)
-                lat = []
+                lat, lat_c = [], []
                 for _ in range(reps):
+                    torch.cuda.synchronize()
                     t = time.perf_counter()
                     ctl.solve(x0, 0.0)
                     lat.append(time.perf_counter() - t)
+                x = np.ascontiguousarray(np.float32(x0))
+                u = np.zeros(5, np.float32)
+                xp, up, hh = x.ctypes.data_as(M.PF), u.ctypes.data_as(M.PF), C.c_void_p(ctl.h)
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    rc = L.mppi_solve(hh, xp, 0.0, None, up)
+                    lat_c.append(time.perf_counter() - t)
+                    assert rc == M.MPPI_OK, rc
                 s = torch.cuda.Stream()
                 dx = torch.tensor(np.float32(x0), device="cuda")
                 du = torch.zeros(5, dtype=torch.float32, device="cuda")
+                torch.cuda.synchronize()
                 with torch.cuda.stream(s):
                     for _ in range(10):
                         M.mppi_solve_async(ctl.h, dx.data_ptr(), 0.0, s, du.data_ptr())
@@ -141,10 +164,12 @@ def paper_table1_latency(M, W, reps: int = 300) -> dict:
                     e1.record(s)
                 s.synchronize()
                 row[mode] = [round(float(np.percentile(lat, 50) * 1e3), 4), round(float(np.percentile(lat, 99) * 1e3), 4),
-                             round(e0.elapsed_time(e1) / reps, 4)]
+                             round(float(np.percentile(lat_c, 50) * 1e3), 4), round(e0.elapsed_time(e1) / reps, 4)]
                 ctl.close()
             out[f"K{K}_N20_{names[obj]}"] = row
-    out["columns"] = "p50_ms, p99_ms, device_ms_per_solve"
+    out["columns"] = "p50_ms, p99_ms, c_p50_ms, device_ms_per_solve"
+    out["protocol"] = ("p50/p99: mppi_solve via the Python binding with the device idle at each call; c_p50: the "
+                       "same C-ABI call via ctypes with prebuilt arguments; device: back-to-back solves, CUDA events")
     out["paper_rtx3090_ms"] = 0.4
     return out
 
@@ -166,6 +191,9 @@ def parse():
                     help="batched solves of the fleet per timed step (consecutive control periods)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the serving run (the configured fleet asks for 60 s)")
+    ap.add_argument("--table1-only", action="store_true",
+                    help="print only the single-solve latency at the paper's Table I sizes (one JSON line)")
+    ap.add_argument("--table1-reps", type=int, default=300, help="timed solves per Table I case and column")
     return ap.parse_args()
 
 
@@ -431,6 +459,11 @@ def main():
     dev = torch.cuda.current_device()
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
+    if args.table1_only:
+        from paper_2509_14726_gb300 import workloads as W
+        if rank == 0:
+            print(json.dumps({"paper_table1_single_solve": paper_table1_latency(M, W, args.table1_reps)}))
+        return
 
     items = workload(rank, args.drones)
     t0 = 0.3
@@ -614,7 +647,7 @@ def main():
         # the paper's solve size (Table I: 8192 samples, horizon 20, dt 0.03,
         # lambda 0.01; 2048 samples onboard): host-synchronous mppi_solve
         # latency, and device time per solve back to back
-        plain["paper_table1_single_solve"] = paper_table1_latency(M, W)
+        plain["paper_table1_single_solve"] = paper_table1_latency(M, W, args.table1_reps)
 
     # ---- closed-loop comparison of the objectives (Sec. V-A protocol) ----
     closed = None

@@ -74,8 +74,25 @@ enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
  *           solves: the block needs 16 N_cap x (block x samples_per_thread)
  *           bytes more shared memory (20 for contouring), at most 200 KB
  *           in all (MPPI_ERR_ARG beyond); mppi_get_noise / mppi_set_noise
- *           return MPPI_ERR_ARG. */
-enum { MPPI_NOISEGEN_KERNEL = 0, MPPI_NOISEGEN_FUSED = 1, MPPI_NOISEGEN_REGEN = 2, MPPI_NOISEGEN_SMEM = 3 };
+ *           return MPPI_ERR_ARG;
+ *   AHEAD:  the Philox pass of KERNEL, run after each single solve
+ *           (mppi_solve, mppi_solve_async) for the next iteration's counters,
+ *           behind the event that u0 waits for: a controller that solves once
+ *           per control period does not wait for its draw.  The draws and
+ *           every result are those of KERNEL, bit for bit.  After a solve,
+ *           mppi_get_noise returns the normals the next solve will use.  A
+ *           change of shape, mppi_import_state or a batch solve (which draws
+ *           before its rollout, as KERNEL does) makes the next single solve
+ *           draw first again.  Issue a handle's solves on one stream, or
+ *           order the streams.  Not for the server or the allocation-free
+ *           solve (MPPI_ERR_ARG). */
+enum {
+  MPPI_NOISEGEN_KERNEL = 0,
+  MPPI_NOISEGEN_FUSED = 1,
+  MPPI_NOISEGEN_REGEN = 2,
+  MPPI_NOISEGEN_SMEM = 3,
+  MPPI_NOISEGEN_AHEAD = 4
+};
 /* accumulation of the K-sample weighted update sum (Eq. 5) */
 enum { MPPI_ACC_KAHAN32 = 0, MPPI_ACC_F64 = 1, MPPI_ACC_F32 = 2 };
 enum { MPPI_RULE_OFF = 0, MPPI_RULE_TIME_ALIGNED = 1, MPPI_RULE_SAME_INDEX = 2 };

@@ -124,6 +124,10 @@ struct mppi_s {
   HostIO io;
   cudaEvent_t ev_u0 = nullptr;
   bool ext_noise_pending = false;
+  // MPPI_NOISEGEN_AHEAD: the noise buffer holds the normals of the state's
+  // current iteration (drawn after the previous solve, recorded by ev_ahead)
+  bool ahead_ready = false;
+  cudaEvent_t ev_ahead = nullptr;
 };
 
 struct mppi_batch_s;
@@ -213,7 +217,7 @@ int validate(const mppi_model_t* m, const mppi_params_t* p, const mppi_track_t* 
   if (p->noise_dtype != MPPI_NOISE_F32 && p->noise_dtype != MPPI_NOISE_BF16)
     return fail(MPPI_ERR_ARG, "unknown noise dtype");
   if (p->accum < 0 || p->accum > 2) return fail(MPPI_ERR_ARG, "unknown accumulation mode");
-  if (p->noise_gen < MPPI_NOISEGEN_KERNEL || p->noise_gen > MPPI_NOISEGEN_SMEM)
+  if (p->noise_gen < MPPI_NOISEGEN_KERNEL || p->noise_gen > MPPI_NOISEGEN_AHEAD)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p->noise_gen == MPPI_NOISEGEN_REGEN && p->noise_dtype != MPPI_NOISE_F32)
     return fail(MPPI_ERR_ARG, "regenerated noise is never stored: it has no bfloat16 form");
@@ -607,7 +611,8 @@ int mppi_create(const mppi_model_t* model, const mppi_params_t* params, const mp
     return cleanup(fail(MPPI_ERR_CUDA, "upload failed"));
   if ((rc = upload_tiles(h))) return cleanup(rc);
   if ((rc = hostio_alloc(h->io, 1))) return cleanup(rc);
-  if (cudaEventCreateWithFlags(&h->ev_u0, cudaEventDisableTiming) != cudaSuccess)
+  if (cudaEventCreateWithFlags(&h->ev_u0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_ahead, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(fail(MPPI_ERR_CUDA, "event creation failed"));
   *out = h;
   return MPPI_OK;
@@ -632,6 +637,7 @@ int mppi_destroy(mppi_handle h) {
     }
   }
   if (h->ev_u0) cudaEventDestroy(h->ev_u0);
+  if (h->ev_ahead) cudaEventDestroy(h->ev_ahead);
   hostio_free(h->io);
   if (h->d_tiles) cudaFree(h->d_tiles);
   if (h->slab) cudaFree(h->slab);
@@ -657,6 +663,7 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
   CU(cudaMemcpy(h->d_desc, &h->hd, sizeof h->hd, cudaMemcpyHostToDevice));
   int rc = upload_tiles(h);
   if (rc) return rc;
+  h->ahead_ready = false;  // the normals drawn ahead have the old shape
   ++h->version;
   return MPPI_OK;
 }
@@ -664,17 +671,35 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
 static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   const SolveDesc& d = h->hd;
   int gen = 0;  // caller noise is already stored: the rollout loads it
+  const bool ahead = d.noise_gen == MPPI_NOISEGEN_AHEAD;
+  if (ahead) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));  // the draw may sit on another stream
   if (h->ext_noise_pending) {
     h->ext_noise_pending = false;
+  } else if (ahead) {
+    // drawn after the previous solve, unless something moved the counters since
+    if (!h->ahead_ready)
+      CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample, d.N));
   } else if (d.noise_gen != MPPI_NOISEGEN_KERNEL) {
     gen = d.noise_gen;
   } else {
-    CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample));
+    CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample, d.N));
   }
   const uint32_t smem =
       rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles), gen, d.ref_rows);
   CU(launch_rollout(d.objective, d.noise_bf16, h->d_desc, h->d_tiles, d.n_tiles, h->block, smem, io, s, gen,
                     d.rotor));
+  h->ahead_ready = false;
+  return MPPI_OK;
+}
+
+// MPPI_NOISEGEN_AHEAD, after the solve's own kernels: the normals of the next
+// iteration (the counter the solve advanced), off the path to u0
+static int draw_ahead(mppi_handle h, cudaStream_t s) {
+  const SolveDesc& d = h->hd;
+  if (d.noise_gen != MPPI_NOISEGEN_AHEAD) return MPPI_OK;
+  CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample, d.N));
+  CU(cudaEventRecord(h->ev_ahead, s));
+  h->ahead_ready = true;
   return MPPI_OK;
 }
 
@@ -693,6 +718,7 @@ int mppi_solve(mppi_handle h, const float x0[13], double t0, void* stream, float
   if (rc) return rc;
   CU(cudaEventRecord(h->ev_u0, s));
   if (h->hd.objective == MPPI_OBJ_GATE) CU(launch_nominal(h->d_desc, h->d_which, 1, s));
+  if ((rc = draw_ahead(h, s))) return rc;
   CU(cudaEventSynchronize(h->ev_u0));
   for (int i = 0; i < kNU; ++i) u0_out[i] = ((volatile float*)h->io.u0)[i];
   const int st = ((volatile int32_t*)h->io.status)[0];
@@ -723,7 +749,7 @@ int mppi_solve_async(mppi_handle h, const float* d_x0, double t0, void* stream, 
   int rc = enqueue_single(h, io, s);
   if (rc) return rc;
   if (h->hd.objective == MPPI_OBJ_GATE) CU(launch_nominal(h->d_desc, h->d_which, 1, s));
-  return MPPI_OK;
+  return draw_ahead(h, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -765,6 +791,7 @@ int mppi_get_noise(mppi_handle h, float* Z) {
   const SolveDesc& d = h->hd;
   if (d.noise_gen == MPPI_NOISEGEN_REGEN || d.noise_gen == MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "this handle keeps no noise in device memory");
+  if (d.noise_gen == MPPI_NOISEGEN_AHEAD) CU(cudaEventSynchronize(h->ev_ahead));
   const size_t nk = (size_t)d.N * d.K;
   std::vector<float> z4(nk * 4), z5(h->nu == 5 ? nk : 0);
   if (d.noise_bf16) {
@@ -864,6 +891,7 @@ int mppi_import_state(mppi_handle h, const void* buf, size_t size) {
   CU(cudaMemcpy(h->hd.U, c, sizeof(float) * h->N_cap * kNU, cudaMemcpyHostToDevice));
   c += sizeof(float) * h->N_cap * kNU;
   CU(cudaMemcpy(h->hd.prevcnt, c, sizeof(int32_t) * h->N_cap, cudaMemcpyHostToDevice));
+  h->ahead_ready = false;  // the iteration counter may have moved
   return MPPI_OK;
 }
 
@@ -901,6 +929,7 @@ int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* strea
   const SolveDesc& d = h->hd;
   if (d.noise_gen == MPPI_NOISEGEN_REGEN || d.noise_gen == MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "this handle has no noise buffer");
+  if (d.noise_gen == MPPI_NOISEGEN_AHEAD) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));
   const size_t nk = (size_t)d.N * d.K;
   const size_t el = d.noise_bf16 ? 2 : 4;
   void* z4 = d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4;
@@ -988,7 +1017,7 @@ static int batch_enqueue_branches(mppi_batch b, const LaunchIO& io, cudaStream_t
     cudaStream_t bs = b->branch_streams[i];
     CU(cudaStreamWaitEvent(bs, b->fork, 0));
     if (g.gen == MPPI_NOISEGEN_KERNEL)
-      CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs, g.nom));
+      CU(launch_noise(b->d_descs, g.d_noise_tiles, g.n_tiles, g.block, g.bf16, bs, g.nom, kMaxN));
     CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, bs, g.gen, g.rot));
     if (i == b->nominal_branch) CU(launch_nominal(b->d_descs, b->d_which, b->n_which, bs));
     CU(cudaEventRecord(b->join[i], bs));
@@ -1027,7 +1056,8 @@ static int capture_dev_graph(mppi_batch b, const float* x0, const double* t0, fl
 }
 
 static int batch_enqueue(mppi_batch b, const LaunchIO& io, cudaStream_t s) {
-  for (const auto& g : b->noise_groups) CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom));
+  for (const auto& g : b->noise_groups)
+    CU(launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom, kMaxN));
   for (const auto& g : b->rollout_groups)
     CU(launch_rollout(g.objective, g.bf16, b->d_descs, g.d_tiles, g.n_tiles, g.block, g.smem, io, s, g.gen, g.rot));
   return MPPI_OK;
@@ -1095,7 +1125,10 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
     const SolveDesc& d = hs[i]->hd;
-    Key k{d.objective, d.noise_bf16, d.block, d.noise_gen, d.nominal_sample, d.rotor};
+    // a batch draws the normals of noise-ahead handles before the rollout,
+    // as for the separate pass
+    const int gen = d.noise_gen == MPPI_NOISEGEN_AHEAD ? MPPI_NOISEGEN_KERNEL : d.noise_gen;
+    Key k{d.objective, d.noise_bf16, d.block, gen, d.nominal_sample, d.rotor};
     Key kn{0, d.noise_bf16, d.block, 0, d.nominal_sample, 0};
     auto find = [](std::vector<std::pair<Key, std::vector<Tile>>>& v, const Key& key) -> int {
       for (size_t j = 0; j < v.size(); ++j)
@@ -1107,8 +1140,8 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
     if ((int)rsmem.size() < (int)rg.size()) rsmem.push_back(0);
     rsmem[gi] =
         std::max(rsmem[gi], rollout_smem_bytes(d.N, d.objective, d.S, tile_samples(d), merge_cap(d.n_tiles),
-                                               d.noise_gen, d.ref_rows));
-    const int gn = d.noise_gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
+                                               gen, d.ref_rows));
+    const int gn = gen != MPPI_NOISEGEN_KERNEL ? -1 : find(ng, kn);
     for (int t = 0; t < d.n_tiles; ++t) {
       rg[gi].second.push_back(Tile{i, t * tile_samples(d)});
       if (gn >= 0) ng[gn].second.push_back(Tile{i, t * tile_samples(d)});
@@ -1226,6 +1259,9 @@ static int batch_check(mppi_batch b) {
     if (b->hs[i]->version != b->versions[i]) return fail(MPPI_ERR_ARG, "handle %d changed shape since the batch was planned", i);
   for (int i = 0; i < b->n; ++i)
     if (b->hs[i]->ext_noise_pending) return fail(MPPI_ERR_ARG, "caller noise is only supported for single solves");
+  // the batch draws its own normals and moves every counter on: what a
+  // noise-ahead handle drew after its last single solve is stale after it
+  for (int i = 0; i < b->n; ++i) b->hs[i]->ahead_ready = false;
   return MPPI_OK;
 }
 
@@ -1283,7 +1319,7 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
   for (int it = 0; it < n_iters && status == MPPI_OK; ++it) {
     cudaEventRecord(ev[0], s);
     for (const auto& g : b->noise_groups)
-      if (launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom) != cudaSuccess)
+      if (launch_noise(b->d_descs, g.d_tiles, g.n_tiles, g.block, g.bf16, s, g.nom, kMaxN) != cudaSuccess)
         status = MPPI_ERR_CUDA;
     cudaEventRecord(ev[1], s);
     for (int obj = 0; obj < 3; ++obj) {

@@ -8,6 +8,7 @@
 //                    solve reads (Sec. IV-A).
 //   test kernels     Philox words, normals and plain rollouts of given
 //                    sequences, for the parity tests.
+#include <algorithm>
 #include <atomic>
 
 #include "mppi_rollout.cuh"
@@ -46,7 +47,10 @@ int rollout_max_block() { return MPPI_ROLLOUT_MIN_BLOCKS > 0 ? 128 : kMaxBlock; 
 // K1: noise
 // ---------------------------------------------------------------------------
 // NOM: the launch holds solves whose sample 0 is the unperturbed nominal
-// (a separate instance, so that the common launch carries no test for it)
+// (a separate instance, so that the common launch carries no test for it).
+// Block (x, y) draws tile x's normals for the y-th of gridDim.y equal spans
+// of the horizon: a launch of few tiles (one small solve) is split along k so
+// that it still fills the GPU; a batch of many tiles runs one span.
 template <int BF16, int NOM>
 __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __restrict__ descs,
                                                           const Tile* __restrict__ tiles) {
@@ -54,6 +58,9 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
   const SolveDesc& d = descs[tile.solve];
   const int K = d.K, N = d.N;
   if (d.ext_noise || threadIdx.x >= d.block) return;
+  const int span = (N + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int k_begin = (int)blockIdx.y * span, k_end = min(N, k_begin + span);
+  if (k_begin >= k_end) return;
   const uint32_t iter = d.st->iter;
   const bool five = d.nu == 5;
   // the thread's samples: m0 + tid + r block, r < samples per thread
@@ -62,7 +69,7 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
     if (m >= K) return;
     if (NOM && m == 0 && d.nominal_sample) {
       // the nominal candidate (Eq. 3 with du = 0) is stored as zero normals
-      for (int k = 0; k < N; ++k) {
+      for (int k = k_begin; k < k_end; ++k) {
         const size_t idx = (size_t)k * K;
         if (BF16) {
           d.Zb[idx] = make_uint2(0u, 0u);
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
       continue;
     }
 #pragma unroll kNoiseUnroll
-    for (int k = 0; k < N; ++k) {
+    for (int k = k_begin; k < k_end; ++k) {
       const float4 z = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
       const size_t idx = (size_t)k * K + m;
       if (BF16) {
@@ -247,16 +254,31 @@ __global__ void rollout_states_kernel(ModelRegs M, RotorRegs R, StepConsts SC, i
 // host-side launch helpers
 // ---------------------------------------------------------------------------
 
+// spans of the horizon per tile: enough blocks for two per SM, at most one
+// span per step of the longest horizon
+static int noise_spans(int n_tiles, int N_max) {
+  static const int n_sm = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 0;
+    (void)cudaGetLastError();
+    return v > 0 ? v : 1;
+  }();
+  const int want = (2 * n_sm + n_tiles - 1) / n_tiles;
+  return std::max(1, std::min(want, std::max(1, N_max)));
+}
+
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
-                         cudaStream_t s, int nominal) {
+                         cudaStream_t s, int nominal, int N_max) {
   if (n_tiles <= 0) return cudaSuccess;
   (void)cudaGetLastError();
+  const dim3 grid((unsigned)n_tiles, (unsigned)noise_spans(n_tiles, N_max));
   if (bf16)
-    nominal ? noise_kernel<1, 1><<<n_tiles, block, 0, s>>>(descs, tiles)
-            : noise_kernel<1, 0><<<n_tiles, block, 0, s>>>(descs, tiles);
+    nominal ? noise_kernel<1, 1><<<grid, block, 0, s>>>(descs, tiles)
+            : noise_kernel<1, 0><<<grid, block, 0, s>>>(descs, tiles);
   else
-    nominal ? noise_kernel<0, 1><<<n_tiles, block, 0, s>>>(descs, tiles)
-            : noise_kernel<0, 0><<<n_tiles, block, 0, s>>>(descs, tiles);
+    nominal ? noise_kernel<0, 1><<<grid, block, 0, s>>>(descs, tiles)
+            : noise_kernel<0, 0><<<grid, block, 0, s>>>(descs, tiles);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -46,9 +46,11 @@ cudaError_t configure_kernels();
 // largest block the rollout kernel was compiled for
 int rollout_max_block();
 
-// nominal: every solve of the launch has nominal_sample set (sample 0 is stored as zeros)
+// nominal: every solve of the launch has nominal_sample set (sample 0 is stored as zeros);
+// N_max: the longest horizon among the launch's solves (a launch of few tiles
+// is split along the horizon)
 cudaError_t launch_noise(const SolveDesc* descs, const Tile* tiles, int n_tiles, int block, int bf16,
-                         cudaStream_t s, int nominal);
+                         cudaStream_t s, int nominal, int N_max);
 cudaError_t launch_rollout(int objective, int bf16, const SolveDesc* descs, const Tile* tiles, int n_tiles,
                            int block, uint32_t smem, LaunchIO io, cudaStream_t s, int gen, int rotor);
 cudaError_t launch_nominal(const SolveDesc* descs, const int32_t* which, int n, cudaStream_t s);

@@ -136,6 +136,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
   if (block < 32 || block > kMaxBlock || block % 32) return fail(MPPI_ERR_ARG, "block must be a multiple of 32 in [32, 512]");
   if (p.K < 1 || p.N < 1 || p.N > MPPI_MAX_N) return fail(MPPI_ERR_ARG, "K or N out of range");
   if (!(p.dt > 0) || !(p.lambda > 0)) return fail(MPPI_ERR_ARG, "dt and lambda must be positive");
+  if (p.noise_gen == MPPI_NOISEGEN_AHEAD) return fail(MPPI_ERR_ARG, "noise drawn ahead needs a handle (it outlives the call)");
   if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "unknown noise generation mode");
   if (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32)
@@ -235,7 +236,7 @@ extern "C" int mppi_solve_noalloc(const mppi_model_t* model, const mppi_params_t
       launch_gate_frames(d_track->gates, d_track->n_gates, const_cast<GateF*>(d.gframes), s) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "gate frame launch failed");
   if (d.noise_gen == MPPI_NOISEGEN_KERNEL &&
-      launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s, d.nominal_sample) != cudaSuccess)
+      launch_noise(d_desc, d_tiles, d.n_tiles, block, bf16, s, d.nominal_sample, d.N) != cudaSuccess)
     return fail(MPPI_ERR_CUDA, "noise kernel launch failed");
   LaunchIO io;
   memset(&io, 0, sizeof io);

@@ -199,7 +199,7 @@ __device__ __forceinline__ int gate_slot(int idx, int n, int closed) {
 // shared-memory layout of the rollout kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_ref, off_e, off_j, off_merge, off_z, total;
+  uint32_t off_U, off_prev, off_gates, off_path, off_xref, off_ref, off_e, off_j, off_merge, off_fin, off_z, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -232,6 +232,8 @@ __host__ __device__ inline SmemLayout smem_layout(int N, int objective, int S, i
   L.off_z = o;  // [N][tile] float4 normals, then [N][tile] 5th normals (contouring)
   if (gen == MPPI_NOISEGEN_SMEM)
     o += align16((uint32_t)N * tile * 16u) + (objective == MPPI_OBJ_CONTOUR ? align16((uint32_t)N * tile * 4u) : 0u);
+  L.off_fin = o;  // the final merge's sums of Eq. 5, [N][5] pairs (last block only)
+  o += align16((uint32_t)N * kNU * 8u);
   L.total = o;
   return L;
 }
@@ -309,27 +311,45 @@ struct MergeIn {
   const double* P;   // [n][NNU] (float2 hi/lo or double)
 };
 
+// PRE: partials of the thread's first output requested up front (0: none;
+// the instances that would spill with them leave them out)
+template <int PRE>
 __device__ inline void merge_partials(const SolveDesc& d, const MergeIn in, int n, int NNU, double* out_m, double* out_S,
                                double* out_P, double* scale_s, double* red, int f64) {
   if (!f64) {
     // binary32 minimum and scales; S and P as compensated (hi, lo) pairs
     float* redf = reinterpret_cast<float*>(red);
     float* scale_f = reinterpret_cast<float*>(scale_s);
-    float mloc = INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) mloc = fminf(mloc, (float)__ldcg(in.m + i));
+    // One round trip to L2 for the common case: the thread's own (m_i, S_i)
+    // and the first PRE partials of its first output are requested before
+    // the first reduction, and arrive while the minimum and the scales are
+    // formed.  The sums keep the index order of the loops below.
+    constexpr int kPre = PRE > 0 ? PRE : 1;
+    float2 pre[kPre];
+    if (PRE > 0 && (int)threadIdx.x < NNU) {
+#pragma unroll
+      for (int t = 0; t < kPre; ++t)
+        pre[t] = t < n ? unpack2(__ldcg(in.P + (size_t)t * NNU + threadIdx.x)) : make_float2(0.f, 0.f);
+    }
+    const bool own = PRE > 0 && (int)threadIdx.x < n;
+    const float m_own = own ? (float)__ldcg(in.m + threadIdx.x) : INFINITY;
+    const float2 S_own = own ? unpack2(__ldcg(in.S + threadIdx.x)) : make_float2(0.f, 0.f);
+    float mloc = m_own;
+    for (int i = threadIdx.x + (PRE > 0 ? blockDim.x : 0); i < n; i += blockDim.x)
+      mloc = fminf(mloc, (float)__ldcg(in.m + i));
     const float mm = block_min_f(mloc, redf);
     float sh = 0.f, sl = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float mi = (float)__ldcg(in.m + i);
+      const float mi = own && i == (int)threadIdx.x ? m_own : (float)__ldcg(in.m + i);
       const float sc = (isinf(mm) || isinf(mi)) ? 0.f : expf(-(mi - mm) * d.inv_lambda);
       scale_f[i] = sc;
-      const float2 Si = unpack2(__ldcg(in.S + i));
+      const float2 Si = own && i == (int)threadIdx.x ? S_own : unpack2(__ldcg(in.S + i));
       const float p = Si.x * sc;
       add2(sh, sl, p, fmaf(Si.x, sc, -p) + Si.y * sc);
     }
     block_sum2_f(sh, sl, redf);  // its barriers make scale_f visible
-    // partials are requested 8 at a time (one L2 round trip per 8 instead of
-    // per partial) and summed in index order
+    // further partials are requested 8 at a time (one L2 round trip per 8
+    // instead of per partial) and summed in index order
     auto acc_one = [&](float& hi, float& lo, float2 v, float sc) {
       const float p = v.x * sc;
       float t, e;
@@ -340,6 +360,12 @@ __device__ inline void merge_partials(const SolveDesc& d, const MergeIn in, int 
     for (int o = threadIdx.x; o < NNU; o += blockDim.x) {
       float hi = 0.f, lo = 0.f;
       int i = 0;
+      if (PRE > 0 && o == (int)threadIdx.x) {
+#pragma unroll
+        for (int t = 0; t < kPre; ++t)
+          if (t < n) acc_one(hi, lo, pre[t], scale_f[t]);
+        i = min(n, kPre);
+      }
       for (; i + 8 <= n; i += 8) {
         float2 v[8];
 #pragma unroll
@@ -1103,6 +1129,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   }
 
   // ---- two-level merge: last block of each group, then last group ----
+  constexpr int kMergePre = (GEN == 0 && ROT == 0) ? 8 : 0;
   const int T = d.n_tiles;
   const int G = group_size_for(T);
   const int n_groups = (T + G - 1) / G;
@@ -1123,7 +1150,7 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   double* gP = d.part_P + (size_t)T * NNU;
   if (n_groups > 1) {
     MergeIn in{d.part_m + grp * G, d.part_S + grp * G, d.part_P + (size_t)grp * G * NNU};
-    merge_partials(d, in, gsize, NNU, gm + grp, gS + grp, gP + (size_t)grp * NNU, sMerge, red, f64);
+    merge_partials<kMergePre>(d, in, gsize, NNU, gm + grp, gS + grp, gP + (size_t)grp * NNU, sMerge, red, f64);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -1139,6 +1166,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
   }
   // final merge -> U*_new = U* + P / S
   {
+    // timeouts counted by any block of this solve: each block counts before
+    // its ticket, so the count is complete here; requested now, used at the end
+    const int32_t timeouts = tid == 0 ? *reinterpret_cast<volatile const int32_t*>(&st->timeouts) : 0;
     MergeIn in;
     int n;
     if (n_groups > 1) {
@@ -1148,8 +1178,9 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       in = MergeIn{d.part_m, d.part_S, d.part_P};
       n = T;
     }
-    double* fP = gP + (size_t)n_groups * NNU;  // scratch row for the final sums
-    merge_partials(d, in, n, NNU, &s_m, &s_S, fP, sMerge, red, f64);
+    // the final sums stay in shared memory
+    double* fP = reinterpret_cast<double*>(smem + Ls.off_fin);
+    merge_partials<kMergePre>(d, in, n, NNU, &s_m, &s_S, fP, sMerge, red, f64);
     __threadfence_block();
     __syncthreads();
     const float2 S2 = unpack2(s_S);
@@ -1173,26 +1204,25 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
       }
       if (j >= nu) v = 0.f;
       d.unew[o] = v;
+      sU[o] = v;  // U*_new replaces U* here (each entry is this thread's own)
       if (k == 0) u0o[j] = v;
     }
     __syncthreads();
-    __threadfence();
     // warm start: shift by one (or keep the sequence), repeat the last row
     // over the whole capacity
     const int shift = d.warm_keep ? 0 : 1;
     for (int o = tid; o < d.N_cap * kNU; o += blockDim.x) {
       const int k = o / kNU, j = o - k * kNU;
       const int src = min(k + shift, N - 1);
-      d.U[o] = d.unew[src * kNU + j];
+      d.U[o] = sU[src * kNU + j];
     }
     if (tid < kNX) st->prev_x0[tid] = x0s[tid];
     if (tid == 0) {
-      const float c0 = d.unew[0];
+      const float c0 = sU[0];
       st->gate0 = st->gate + (OBJ == MPPI_OBJ_GATE ? s_adv : 0);
       st->adv = OBJ == MPPI_OBJ_GATE ? s_adv : 0;
       st->gate = st->gate0;
-      // timeouts counted by any block of this solve (before its ticket)
-      const int32_t to = atomicAdd(&st->timeouts, 0);
+      const int32_t to = timeouts;
       const int status = to != st->timeouts_seen ? MPPI_ERR_TIMEOUT : degenerate ? MPPI_WARN_DEGENERATE : MPPI_OK;
       st->timeouts_seen = to;
       st->status = status;
@@ -1207,12 +1237,12 @@ __global__ void MPPI_ROLLOUT_BOUNDS rollout_kernel(const SolveDesc* __restrict__
         for (int r = 0; r < 4; ++r) {
           const float t0r = hr ? st->rotor[r] : 0.25f * d.hover;
           st->rotor_prev[r] = t0r;
-          st->rotor[r] = clampf(t0r + d.unew[r] * d.dt, d.thrust_min, d.thrust_max);
+          st->rotor[r] = clampf(t0r + sU[r] * d.dt, d.thrust_min, d.thrust_max);
         }
         st->has_rotor = 1;
       }
       if (OBJ == MPPI_OBJ_CONTOUR) {
-        const float a0 = d.unew[4];
+        const float a0 = sU[4];
         st->theta = s_theta0;
         st->v_theta = (double)clampf(s_vth0 + a0 * d.dt, 0.f, d.v_theta_max);
         st->has_theta = 1;

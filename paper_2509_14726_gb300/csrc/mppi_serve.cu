@@ -311,6 +311,8 @@ int mppi_server_add_drone(mppi_server s, const mppi_model_t* model, const mppi_p
   if (p.objective < 0 || p.objective > 2) return sfail(MPPI_ERR_ARG, "unknown objective");
   if (p.noise_dtype != MPPI_NOISE_F32 && p.noise_dtype != MPPI_NOISE_BF16) return sfail(MPPI_ERR_ARG, "noise dtype");
   if (p.accum < 0 || p.accum > 2) return sfail(MPPI_ERR_ARG, "unknown accumulation mode");
+  if (p.noise_gen == MPPI_NOISEGEN_AHEAD)
+    return sfail(MPPI_ERR_ARG, "noise drawn ahead is for single solves: a served drone draws its own");
   if (p.noise_gen < MPPI_NOISEGEN_KERNEL || p.noise_gen > MPPI_NOISEGEN_SMEM ||
       (p.noise_gen == MPPI_NOISEGEN_REGEN && p.noise_dtype != MPPI_NOISE_F32))
     return sfail(MPPI_ERR_ARG, "bad noise generation mode");
@@ -637,7 +639,7 @@ int mppi_server_step(mppi_server s, int32_t* launched) {
   for (size_t q = 0; q < groups.size(); ++q)
     if (groups[q].gen == MPPI_NOISEGEN_KERNEL)
       SCU_UNDO(launch_noise(ddesc, dtiles + goff[q], (int)groups[q].t.size(), groups[q].block, groups[q].bf16, stm,
-                            groups[q].nom));
+                            groups[q].nom, kMaxN));
   for (size_t q = 0; q < groups.size(); ++q)
     SCU_UNDO(launch_rollout(groups[q].obj, groups[q].bf16, ddesc, dtiles + goff[q], (int)groups[q].t.size(),
                             groups[q].block, groups[q].smem, io, stm, groups[q].gen, groups[q].rot));

@@ -20,7 +20,7 @@ LIB_PATH = os.environ.get("MPPI_LIB") or os.path.join(HERE, "lib", "libmppi.so")
 
 MPPI_OK, MPPI_ERR_ARG, MPPI_ERR_OOM, MPPI_ERR_CUDA, MPPI_ERR_TIMEOUT, MPPI_ERR_NOT_ADMITTED, MPPI_WARN_DEGENERATE = range(7)
 NOISE_F32, NOISE_BF16 = 0, 1
-NOISEGEN_KERNEL, NOISEGEN_FUSED, NOISEGEN_REGEN, NOISEGEN_SMEM = 0, 1, 2, 3
+NOISEGEN_KERNEL, NOISEGEN_FUSED, NOISEGEN_REGEN, NOISEGEN_SMEM, NOISEGEN_AHEAD = 0, 1, 2, 3, 4
 NOISEGEN_DEFAULT = NOISEGEN_KERNEL
 ACC_KAHAN32, ACC_F64, ACC_F32 = 0, 1, 2
 F = C.c_float

@@ -1,6 +1,7 @@
 """Noise drawn inside the rollout -- stored (MPPI_NOISEGEN_FUSED) or drawn
-again by the update and never stored (MPPI_NOISEGEN_REGEN) -- against the
-separate Philox pass and against the FP64 oracle.
+again by the update and never stored (MPPI_NOISEGEN_REGEN) -- and noise drawn
+by the separate pass after the previous solve (MPPI_NOISEGEN_AHEAD), against
+the separate Philox pass and against the FP64 oracle.
 
 Both evaluate the same Philox4x32-10 / Box-Muller arithmetic on the same
 counters (Sec. III-B, Eq. 3), so the fused path's stored noise is
@@ -138,7 +139,7 @@ def test_batch_with_mixed_noise_modes(M, use_graph):
     for i, it in enumerate(items):
         sc = W.SolveConfig(objective=it.objective, K=it.K, N=it.N, dt=0.02, drone_id=it.drone_id)
         case = f32_case(W.ModelConfig(), sc, it.track, it.x0)
-        mode = i % 4  # separate pass, fused, regenerated, kept in shared memory
+        mode = i % 5  # separate pass, fused, regenerated, kept in shared memory, drawn ahead
         g1 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         g2 = M.Controller(case.mc, case.sc, case.tr, noise_gen=mode)
         trip.append((g1, g2, case))
@@ -249,5 +250,86 @@ def test_noise_kept_in_shared_memory(M):
     with pytest.raises(M.MppiError) as e:
         M.Controller(big.mc, big.sc, big.tr, noise_gen=M.NOISEGEN_SMEM)
     assert e.value.code == M.MPPI_ERR_ARG
+    a.close()
+    b.close()
+
+
+def _equal_solves(a, b, x0, t0):
+    ua, _ = a.solve(x0, t0)
+    ub, _ = b.solve(x0, t0)
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(a.costs(), b.costs())
+    np.testing.assert_array_equal(a.unew(), b.unew())
+    np.testing.assert_array_equal(a.nominal(), b.nominal())
+    assert a.export_state() == b.export_state()
+
+
+@pytest.mark.parametrize("objective", [0, 1, 2])
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_noise_drawn_ahead_equals_separate(O, M, objective, bf16):
+    """MPPI_NOISEGEN_AHEAD draws the next solve's normals after each solve.
+    Every result is the separate pass's, bit for bit, over consecutive
+    solves, a change of shape, caller noise for one solve and an imported
+    state; after a solve the buffer holds the normals the next solve uses."""
+    case = _case(objective, 3001, 20)
+    kw = dict(noise_dtype=bf16, block=128, K_cap=4096, N_cap=30)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_AHEAD, **kw)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL, **kw)
+    t0 = 0.37
+    x0 = _x0(O, case, t0)
+    ahead = None
+    for rep in range(3):
+        _equal_solves(a, b, x0, t0 + 0.02 * rep)
+        if ahead is not None:
+            # what a drew after its previous solve is what b drew for this one
+            np.testing.assert_array_equal(ahead, b.noise())
+        ahead = a.noise()
+    # a change of shape: the next solve draws first
+    for c in (a, b):
+        c.set_shape(4096, 30)
+    _equal_solves(a, b, x0, t0 + 0.1)
+    if not bf16:
+        # caller noise for one solve, then the draws resume
+        rng = np.random.default_rng(11)
+        z = torch.tensor(rng.standard_normal((30, 4096, 4)).astype(np.float32), device="cuda").contiguous()
+        z5 = torch.tensor(rng.standard_normal((30, 4096)).astype(np.float32), device="cuda").contiguous()
+        for c in (a, b):
+            M.mppi_set_noise(c.h, z.data_ptr(), z5.data_ptr() if objective == 1 else None)
+        _equal_solves(a, b, x0, t0 + 0.12)
+        _equal_solves(a, b, x0, t0 + 0.14)
+    # an imported state moves the iteration counter: the next solve draws first
+    b.solve(x0, t0 + 0.16)
+    a.import_state(b.export_state())
+    _equal_solves(a, b, x0, t0 + 0.18)
+    _equal_solves(a, b, x0, t0 + 0.2)
+    a.close()
+    b.close()
+
+
+def test_noise_drawn_ahead_is_for_single_solves(M):
+    """The server refuses MPPI_NOISEGEN_AHEAD; a batch draws the normals of
+    such a handle itself, and the next single solve draws first again (the
+    batch moved the counter)."""
+    fleet = W.c5_fleet(n_drones=2, distinct_tracks=2)
+    srv = M.Server(len(fleet), 1 << 28, n_slots=1, max_batch=2)
+    d = fleet[0]
+    sc = W.SolveConfig(objective=d.objective, K=1024, N=20, dt=0.02, drone_id=d.drone_id)
+    with pytest.raises(M.MppiError) as e:
+        srv.add_drone(W.ModelConfig(), sc, d.track, 1024, 20, noise_gen=M.NOISEGEN_AHEAD)
+    assert e.value.code == M.MPPI_ERR_ARG
+    srv.close()
+    case = _case(0, 2048, 20)
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_AHEAD)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL)
+    _equal_solves(a, b, case.x0, 0.0)
+    plan_a = M.mppi_batch_create([a.h], use_graph=0)
+    plan_b = M.mppi_batch_create([b.h], use_graph=0)
+    X0 = np.array([case.x0])
+    ua, _ = M.mppi_batch_solve(plan_a, 1, X0, np.zeros(1))
+    ub, _ = M.mppi_batch_solve(plan_b, 1, X0, np.zeros(1))
+    np.testing.assert_array_equal(ua, ub)
+    M.mppi_batch_destroy(plan_a)
+    M.mppi_batch_destroy(plan_b)
+    _equal_solves(a, b, case.x0, 0.02)
     a.close()
     b.close()

@@ -108,6 +108,21 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(M):
     assert b"static maximum" in M.load().mppi_last_error()
 
 
+def test_noalloc_refuses_noise_drawn_ahead(M):
+    """MPPI_NOISEGEN_AHEAD draws for a handle's next solve; a call that keeps
+    nothing between calls refuses it before touching any buffer."""
+    mc, sc, tr, x0 = W.c4_precision()
+    sc.K, sc.N = 1024, 20
+    p = M.make_params(sc, noise_gen=M.NOISEGEN_AHEAD)
+    d_track, keep = _device_track(M, tr)
+    dummy = torch.zeros(1024, dtype=torch.float32, device="cuda")
+    rc = M.load().mppi_solve_noalloc(C.byref(M.make_model(mc)), C.byref(p), C.byref(d_track),
+                                     C.c_void_p(dummy.data_ptr()), 0.0, C.c_void_p(dummy.data_ptr()), 0, 0, None,
+                                     C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()))
+    assert rc == M.MPPI_ERR_ARG
+    assert b"noise drawn ahead" in M.load().mppi_last_error()
+
+
 def test_noalloc_fused_noise_equals_separate_pass(M):
     """Noise drawn inside the rollout (stored, or drawn again by the update)
     gives the two-kernel result to binary32 rounding (the draws are
