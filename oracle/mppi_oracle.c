@@ -28,7 +28,9 @@
  *     gravity (0, 0, -g); q is renormalised after every RK4 step
  *   - Philox4x32-10 (Salmon et al., SC'11) with key (seed, drone) and counter
  *     (sample, step, iteration, block); uniforms ((x >> 8) + 1) * 2^-24 in
- *     (0, 1]; Box-Muller turns (x0, x1) and (x2, x3) into four normals
+ *     (0, 1]; Box-Muller turns (x0, x1) and (x2, x3) into four normals;
+ *     the 5th (progress) normals of steps 4j .. 4j+3 are the four normals of
+ *     block 1 at step 4j, in order
  *   - inputs are clamped to their box; the clamped samples are rolled out and
  *     averaged; the feasibility penalty acts on body rate and altitude
  *   - warm start shifts the new nominal by one step and repeats the last row
@@ -652,8 +654,9 @@ int or_solve(const or_model* md, const or_params* pr, const or_track* tr, or_sta
         or_normals4(pr->seed, pr->drone_id, (uint32_t)m, (uint32_t)k, st->iter, 0u, z4);
         for (int j = 0; j < 4; ++j) z[j] = z4[j];
         if (nu == 5) {
-          or_normals4(pr->seed, pr->drone_id, (uint32_t)m, (uint32_t)k, st->iter, 1u, z4);
-          z[4] = z4[0];
+          /* one block-1 draw serves four consecutive steps */
+          or_normals4(pr->seed, pr->drone_id, (uint32_t)m, (uint32_t)(k & ~3), st->iter, 1u, z4);
+          z[4] = z4[k & 3];
         }
       }
       if (out && out->Z)

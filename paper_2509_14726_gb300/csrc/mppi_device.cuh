@@ -188,6 +188,16 @@ __device__ __forceinline__ float4 normals4(uint32_t seed, uint32_t drone, uint32
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The 5th (progress) normal of (sample m, step k), contouring: the four
+// normals of block 1 at step 4 floor(k / 4) serve steps 4j .. 4j+3 in order,
+// so this draws one Philox block and the one Box-Muller pair step k needs.
+__device__ __forceinline__ float normal5(uint32_t seed, uint32_t drone, uint32_t m, uint32_t k, uint32_t iter) {
+  const uint4 x = philox4x32_10(make_uint4(m, k & ~3u, iter, 1u), seed, drone);
+  const bool hi = (k & 2u) != 0u;
+  const float2 z = box_muller(hi ? x.z : x.x, hi ? x.w : x.y);
+  return (k & 1u) ? z.y : z.x;
+}
+
 // --------------------------------------------------------------------------
 // small helpers
 // --------------------------------------------------------------------------

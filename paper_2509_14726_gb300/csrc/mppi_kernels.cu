@@ -94,14 +94,23 @@ __global__ void __launch_bounds__(kMaxBlock) noise_kernel(const SolveDesc* __res
       } else {
         d.Z4[idx] = z;
       }
-      if (five) {
-        // the 5th normal is the first output of block 1 (one Box-Muller pair)
-        const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
-        const float z5 = box_muller(x5.x, x5.y).x;
-        if (BF16)
-          d.Z5b[idx] = __float2bfloat16_rn(z5);
-        else
-          d.Z5[idx] = z5;
+      if (five && (k == k_begin || (k & 3) == 0)) {
+        // contouring's 5th normals of steps 4j .. 4j+3 (those in this span):
+        // the four normals of one block-1 draw (the values normal5 returns),
+        // stored at once so that nothing stays live across the steps
+        const int k4 = k & ~3;
+        const float4 z5 = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k4, iter, 1u);
+        const float v5[4] = {z5.x, z5.y, z5.z, z5.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = k4 + t;
+          if (j < k || j >= k_end) continue;
+          const size_t jdx = (size_t)j * K + m;
+          if (BF16)
+            d.Z5b[jdx] = __float2bfloat16_rn(v5[t]);
+          else
+            d.Z5[jdx] = v5[t];
+        }
       }
     }
   }

@@ -269,10 +269,7 @@ __device__ __forceinline__ void gen_noise(const SolveDesc& d, uint32_t iter, int
   const size_t idx = (size_t)k * d.K + m;
   float4 v = normals4(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter, 0u);
   float z5 = 0.f;
-  if (five) {
-    const uint4 x5 = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)k, iter, 1u), d.seed, d.drone_id);
-    z5 = box_muller(x5.x, x5.y).x;
-  }
+  if (five) z5 = normal5(d.seed, d.drone_id, (uint32_t)m, (uint32_t)k, iter);
   if (m == 0 && d.nominal_sample) {  // Eq. 3 with du = 0
     v = make_float4(0.f, 0.f, 0.f, 0.f);
     z5 = 0.f;

@@ -9,8 +9,8 @@ implementation shows up as a disagreement:
 
   Eq. 3   samples U^m = clamp(U* + sigma z^m), z from Philox4x32-10
           (Salmon et al., SC'11) and Box-Muller, counter (m, k, iteration,
-          block), key (seed, drone); the 5th (progress) normal is the first
-          output of block 1
+          block), key (seed, drone); the 5th (progress) normals of steps
+          4j .. 4j+3 are the four outputs of block 1 at step 4j
   Eq. 2   quadrotor with collective thrust and body-rate command: p' = v,
           v' = (c/m) R(q) e_z - g e_z, q' = q (x) (0, w) / 2,
           w' = k_w (w_cmd - w) - J^-1 (w x J w); classical RK4, the input
@@ -283,7 +283,7 @@ class NumpyController:
         for k in range(N):
             Z[:, k, 0:4] = normals(sc.seed, sc.drone_id, np.arange(K), k, self.it, 0)
             if nu == 5:
-                Z[:, k, 4] = normals(sc.seed, sc.drone_id, np.arange(K), k, self.it, 1)[:, 0]
+                Z[:, k, 4] = normals(sc.seed, sc.drone_id, np.arange(K), k - k % 4, self.it, 1)[:, k % 4]
         Us = np.clip(U[None] + np.asarray(sc.sigma) * Z, np.asarray(mc.u_min), np.asarray(mc.u_max))
         Us[:, :, nu:] = 0.0
         theta0, vth0, xref = 0.0, 0.0, None

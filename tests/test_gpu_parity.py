@@ -70,6 +70,25 @@ def test_normals_within_binary32_rounding(O, M):
     assert np.all(err <= 6 * 2.0 ** -23 * np.abs(ref) + 1e-7), err.max()
 
 
+@pytest.mark.parametrize("K,N,noise_gen", [(300, 11, 0), (40000, 11, 0), (300, 11, 1), (5000, 23, 1)])
+def test_fifth_normal_stream(O, M, K, N, noise_gen):
+    """Contouring's 5th normals: step k uses normal k mod 4 of Philox block 1
+    at step 4 floor(k / 4).  Checked on every step against the oracle's draw,
+    for the separate pass split along the horizon (few tiles) and in one span
+    (many tiles), and for the draw inside the rollout."""
+    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_CONTOUR)
+    sc.K, sc.N = K, N
+    case = f32_case(mc, sc, tr, x0)
+    gpu = M.Controller(case.mc, case.sc, case.tr, noise_gen=noise_gen)
+    gpu.solve(case.x0, 0.0)
+    Z5 = gpu.noise()[:, :, 4]
+    ms = sorted(set(list(range(0, 5)) + list(range(0, K, max(1, K // 97))) + [K - 1]))
+    ref = np.array([[O.normals4(sc.seed, sc.drone_id, m, k - k % 4, 0, 1)[k % 4] for m in ms] for k in range(N)])
+    err = np.abs(Z5[:, ms] - ref)
+    assert np.all(err <= 6 * 2.0 ** -23 * np.abs(ref) + 1e-7), err.max()
+    gpu.close()
+
+
 # ---------------------------------------------------------------------------
 # the model: RK4 rollouts of given sequences
 # ---------------------------------------------------------------------------

@@ -78,6 +78,8 @@ MUTATIONS = [
      "for (int i = 0; i < 3; ++i) Tn[i] /= n;", "(void)n;"),
     ("contouring state terms on the start state",
      "double e[3] = {xn[0] - P[0], xn[1] - P[1], xn[2] - P[2]};", "double e[3] = {x[0] - P[0], x[1] - P[1], x[2] - P[2]};"),
+    ("5th normal drawn per step instead of four steps per draw",
+     "(uint32_t)(k & ~3), st->iter, 1u, z4);", "(uint32_t)k, st->iter, 1u, z4);"),
     ("samples not clamped",
      "u[j] = clampd(Unom[OR_NU * k + j] + pr->sigma[j] * z[j], md->u_min[j], md->u_max[j]);",
      "u[j] = Unom[OR_NU * k + j] + pr->sigma[j] * z[j];"),

@@ -684,6 +684,21 @@ def test_noise_stream_and_iteration_counter(oracle_mod):
         np.testing.assert_array_equal(r1["Z"][k, m, :4], oracle_mod.normals4(sc.seed, sc.drone_id, m, k, 1, 0))
 
 
+def test_fifth_normals_take_four_steps_from_one_draw(oracle_mod):
+    """Contouring's 5th normals of steps 4j .. 4j+3 are the four normals of
+    Philox block 1 at step 4j, in order: each block-1 draw is used once, and
+    the stream of a sample never repeats a value across steps."""
+    mc, sc, tr, x0 = W.c2_full_scale(W.OBJ_CONTOUR)
+    sc.K, sc.N = 8, 10
+    r = oracle_mod.OracleController(mc, sc, tr).solve(x0, 0.0, want_Z=True)
+    for m in range(sc.K):
+        col = r["Z"][:, m, 4]
+        for j in range(0, sc.N, 4):
+            draw = oracle_mod.normals4(sc.seed, sc.drone_id, m, j, 0, 1)
+            np.testing.assert_array_equal(col[j:j + 4], draw[: len(col[j:j + 4])])
+        assert len(set(col.tolist())) == sc.N
+
+
 def test_plant_crossing_advances_the_gate_and_shifts_counts(oracle_mod):
     mc, sc, tr, x0 = _small_case()
     ctl = oracle_mod.OracleController(mc, sc, tr)
