@@ -150,10 +150,12 @@ def test_c1_first_solve(O, M):
     gpu.close()
 
 
-@pytest.mark.parametrize("K,N,block", [(1, 1, 32), (33, 3, 32), (1000, 13, 128), (3000, 20, 64), (5000, 7, 128), (20000, 5, 64)])
+@pytest.mark.parametrize("K,N,block", [(1, 1, 32), (33, 3, 32), (1000, 13, 128), (3000, 20, 64), (5000, 7, 128),
+                                     (20000, 5, 64), (2100, 30, 64), (8192, 25, 128)])
 def test_ragged_tiles_and_merge_levels(O, M, K, N, block):
     """K not a multiple of the block, one tile, several tiles, and enough
-    tiles for the two-level merge (more than 16)."""
+    tiles for the two-level merge (more than 16), with short and long
+    horizons (one and several of the N x 5 sums per thread)."""
     case = c1_case(K=K, N=N)
     gpu, ora = make_pair(case, block=block)
     gpu.solve(case.x0, 0.0)
