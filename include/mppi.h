@@ -268,7 +268,9 @@ int mppi_get_costs(mppi_handle h, double* J);
  * inside the horizon and step of the first accepted pass (-1: none). */
 int mppi_get_sample_info(mppi_handle h, int32_t* npass, int32_t* first_pass);
 /* Sampled standard normals of the last solve [N][K][5] (the 5th column is
- * only filled for contouring; BF16 storage is widened to float). */
+ * only filled for contouring, where steps 4j .. 4j+3 take the four normals
+ * of block 1 at step 4j; BF16 storage is widened to float).  With
+ * MPPI_NOISEGEN_AHEAD: the normals the next solve will use. */
 int mppi_get_noise(mppi_handle h, float* Z);
 /* Gates passed by each state of the last nominal rollout [N+1]. */
 int mppi_get_passcnt(mppi_handle h, int32_t* passcnt);
