@@ -668,11 +668,24 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
   return MPPI_OK;
 }
 
+// MPPI_NOISEGEN_AHEAD: orders stream s after the handle's pending draw, which
+// may sit on another stream.  A capturing stream is left alone: its graph
+// replays in stream order, and an event recorded outside the capture cannot
+// be waited on inside it.
+static int wait_ahead(mppi_handle h, cudaStream_t s) {
+  if (h->hd.noise_gen != MPPI_NOISEGEN_AHEAD) return MPPI_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s, &cs));
+  if (cs == cudaStreamCaptureStatusNone) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));
+  return MPPI_OK;
+}
+
 static int enqueue_single(mppi_handle h, const LaunchIO& io, cudaStream_t s) {
   const SolveDesc& d = h->hd;
   int gen = 0;  // caller noise is already stored: the rollout loads it
   const bool ahead = d.noise_gen == MPPI_NOISEGEN_AHEAD;
-  if (ahead) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));  // the draw may sit on another stream
+  int rc = wait_ahead(h, s);
+  if (rc) return rc;
   if (h->ext_noise_pending) {
     h->ext_noise_pending = false;
   } else if (ahead) {
@@ -929,7 +942,8 @@ int mppi_set_noise(mppi_handle h, const void* d_Z, const void* d_Z5, void* strea
   const SolveDesc& d = h->hd;
   if (d.noise_gen == MPPI_NOISEGEN_REGEN || d.noise_gen == MPPI_NOISEGEN_SMEM)
     return fail(MPPI_ERR_ARG, "this handle has no noise buffer");
-  if (d.noise_gen == MPPI_NOISEGEN_AHEAD) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));
+  int rc = wait_ahead(h, s);
+  if (rc) return rc;
   const size_t nk = (size_t)d.N * d.K;
   const size_t el = d.noise_bf16 ? 2 : 4;
   void* z4 = d.noise_bf16 ? (void*)d.Zb : (void*)d.Z4;
@@ -1254,22 +1268,27 @@ int mppi_batch_create(int32_t n, const mppi_handle* hs, int32_t use_graph, mppi_
   return MPPI_OK;
 }
 
-static int batch_check(mppi_batch b) {
+static int batch_check(mppi_batch b, cudaStream_t s) {
   for (int i = 0; i < b->n; ++i)
     if (b->hs[i]->version != b->versions[i]) return fail(MPPI_ERR_ARG, "handle %d changed shape since the batch was planned", i);
   for (int i = 0; i < b->n; ++i)
     if (b->hs[i]->ext_noise_pending) return fail(MPPI_ERR_ARG, "caller noise is only supported for single solves");
   // the batch draws its own normals and moves every counter on: what a
-  // noise-ahead handle drew after its last single solve is stale after it
-  for (int i = 0; i < b->n; ++i) b->hs[i]->ahead_ready = false;
+  // noise-ahead handle drew after its last single solve is stale after it.
+  // That draw may still run on another stream: the batch waits for it.
+  for (int i = 0; i < b->n; ++i) {
+    const int rc = wait_ahead(b->hs[i], s);
+    if (rc) return rc;
+    b->hs[i]->ahead_ready = false;
+  }
   return MPPI_OK;
 }
 
 int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* stream, float* u0s_out) {
   if (!b || !x0s || !u0s_out) return fail(MPPI_ERR_ARG, "null argument");
-  int rc = batch_check(b);
-  if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = batch_check(b, s);
+  if (rc) return rc;
   memcpy(b->io.x0, x0s, sizeof(float) * 13 * b->n);
   if (t0s)
     memcpy(b->io.t0, t0s, sizeof(double) * b->n);
@@ -1303,9 +1322,9 @@ int mppi_batch_solve(mppi_batch b, const float* x0s, const double* t0s, void* st
 
 int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out[6]) {
   if (!b || n_iters < 1 || !ms_out) return fail(MPPI_ERR_ARG, "bad arguments");
-  int rc = batch_check(b);
-  if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = batch_check(b, s);
+  if (rc) return rc;
   LaunchIO io;
   memset(&io, 0, sizeof io);
   io.x0 = b->io.d_x0;
@@ -1350,9 +1369,9 @@ int mppi_batch_profile(mppi_batch b, int32_t n_iters, void* stream, float ms_out
 
 int mppi_batch_solve_async(mppi_batch b, const float* d_x0s, const double* d_t0s, void* stream, float* d_u0s) {
   if (!b || !d_x0s || !d_u0s) return fail(MPPI_ERR_ARG, "null argument");
-  int rc = batch_check(b);
-  if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = batch_check(b, s);
+  if (rc) return rc;
   LaunchIO io;
   memset(&io, 0, sizeof io);
   io.x0 = d_x0s;

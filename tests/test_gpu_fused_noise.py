@@ -333,3 +333,30 @@ def test_noise_drawn_ahead_is_for_single_solves(M):
     _equal_solves(a, b, case.x0, 0.02)
     a.close()
     b.close()
+
+
+def test_noise_drawn_ahead_across_streams(O, M):
+    """A noise-ahead handle whose solves move between streams, then into a
+    batch on a third: each call waits for the draw the previous one left
+    running, so every result is the separate pass's, bit for bit."""
+    case = _case(1, 3001, 20)  # contouring: the 5th normals too
+    a = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_AHEAD)
+    b = M.Controller(case.mc, case.sc, case.tr, noise_gen=M.NOISEGEN_KERNEL)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    x0 = case.x0
+    for rep in range(4):
+        ua, _ = a.solve(x0, 0.02 * rep, stream=streams[rep % 2])
+        ub, _ = b.solve(x0, 0.02 * rep)
+        np.testing.assert_array_equal(ua, ub)
+        np.testing.assert_array_equal(a.unew(), b.unew())
+    plan_a = M.mppi_batch_create([a.h], use_graph=1)
+    plan_b = M.mppi_batch_create([b.h], use_graph=1)
+    ua, _ = M.mppi_batch_solve(plan_a, 1, np.array([x0]), np.full(1, 0.1), stream=streams[2])
+    ub, _ = M.mppi_batch_solve(plan_b, 1, np.array([x0]), np.full(1, 0.1))
+    np.testing.assert_array_equal(ua, ub)
+    torch.cuda.synchronize()
+    assert a.export_state() == b.export_state()
+    M.mppi_batch_destroy(plan_a)
+    M.mppi_batch_destroy(plan_b)
+    a.close()
+    b.close()
