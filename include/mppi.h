@@ -83,9 +83,11 @@ enum { MPPI_NOISE_F32 = 0, MPPI_NOISE_BF16 = 1 };
  *           mppi_get_noise returns the normals the next solve will use.  A
  *           change of shape, mppi_import_state or a batch solve (which draws
  *           before its rollout, as KERNEL does) makes the next single solve
- *           draw first again.  Issue a handle's solves on one stream, or
- *           order the streams.  Not for the server or the allocation-free
- *           solve (MPPI_ERR_ARG). */
+ *           draw first again.  A solve, mppi_set_noise or a batch on
+ *           another stream waits for the pending draw (an event); inside a
+ *           stream capture it does not, so capture a handle's solves on one
+ *           stream.  Not for the server or the allocation-free solve
+ *           (MPPI_ERR_ARG). */
 enum {
   MPPI_NOISEGEN_KERNEL = 0,
   MPPI_NOISEGEN_FUSED = 1,
