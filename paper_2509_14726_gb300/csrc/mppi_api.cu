@@ -128,6 +128,8 @@ struct mppi_s {
   // current iteration (drawn after the previous solve, recorded by ev_ahead)
   bool ahead_ready = false;
   cudaEvent_t ev_ahead = nullptr;
+  bool ahead_pending = false;      // ev_ahead records a draw ...
+  cudaStream_t ahead_stream = 0;   // ... enqueued on this stream
 };
 
 struct mppi_batch_s;
@@ -674,6 +676,7 @@ int mppi_set_shape(mppi_handle h, int32_t K, int32_t N) {
 // be waited on inside it.
 static int wait_ahead(mppi_handle h, cudaStream_t s) {
   if (h->hd.noise_gen != MPPI_NOISEGEN_AHEAD) return MPPI_OK;
+  if (!h->ahead_pending || h->ahead_stream == s) return MPPI_OK;  // nothing to wait for, or in order
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(s, &cs));
   if (cs == cudaStreamCaptureStatusNone) CU(cudaStreamWaitEvent(s, h->ev_ahead, 0));
@@ -713,6 +716,8 @@ static int draw_ahead(mppi_handle h, cudaStream_t s) {
   CU(launch_noise(h->d_desc, h->d_tiles, d.n_tiles, h->block, d.noise_bf16, s, d.nominal_sample, d.N));
   CU(cudaEventRecord(h->ev_ahead, s));
   h->ahead_ready = true;
+  h->ahead_pending = true;
+  h->ahead_stream = s;
   return MPPI_OK;
 }
 
