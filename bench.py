@@ -362,7 +362,7 @@ def oracle_parity(items, M, n_parity: int = 6) -> dict:
     t0 = 0.3
     X = start_states(items, t0)
     out = {"bound_nominal": 1e-5, "bound_cost_rel": 1e-4, "per_drone": [], "literal_pass": 0, "literal_miss": 0,
-           "max_rel_J": 0.0, "max_dU": 0.0, "decision_mismatches": 0}
+           "max_rel_J": 0.0, "max_abs_J": 0.0, "max_dU": 0.0, "decision_mismatches": 0}
     for i, it in enumerate(items[:n_parity]):
         mc, sc, tr = W.f32_model(W.ModelConfig()), W.f32_solve(make_cfg(it)), it.track.as_f32()
         x = np.float32(X[i]).astype(np.float64)
@@ -385,6 +385,7 @@ def oracle_parity(items, M, n_parity: int = 6) -> dict:
         out["per_drone"].append(row)
         out["literal_pass" if dU <= 1e-5 else "literal_miss"] += 1
         out["max_rel_J"] = max(out["max_rel_J"], row["max_rel_J"])
+        out["max_abs_J"] = max(out["max_abs_J"], row["max_abs_J"])
         out["max_dU"] = max(out["max_dU"], dU)
         out["decision_mismatches"] += mism
         gpu.close()
@@ -714,9 +715,10 @@ def main():
                         "table_ms": [[t["block"], t["graph_mode"], t["noise_gen"], t["spt"], r4(t["ms"])]
                                      for t in (tuning["table"] or [])]}
         parity_brief = {k: parity[k] for k in ("bound_nominal", "bound_cost_rel", "literal_pass", "literal_miss",
-                                                "max_rel_J", "max_dU", "decision_mismatches")}
+                                                "max_rel_J", "max_abs_J", "max_dU", "decision_mismatches")}
         parity_brief["per_drone"] = [
-            f"{p['drone']}: obj {p['objective']} K {p['K']} N {p['N']}: rel J {p['max_rel_J']:.2g}, |dU| "
+            f"{p['drone']}: obj {p['objective']} K {p['K']} N {p['N']}: rel J {p['max_rel_J']:.2g} "
+            f"(abs {p['max_abs_J']:.2g}), |dU| "
             f"{p['max_dU']:.3g}" + ("" if p["literal"] else f" > 1e-5, binary32 floor {p.get('binary32_floor') or 0:.3g}")
             for p in parity["per_drone"]]
         line = {
