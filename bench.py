@@ -418,7 +418,7 @@ def cpu_baseline(items, budget_s: float, omp: bool = True) -> dict:
     return {"value": steps / used, "unit": "rollout-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{solves} whole solves (drones 0..{solves - 1} of the batch workload, {steps} rollout "
                       f"steps, {used:.1f} s, {'OpenMP over samples, ' if omp else ''}{cores} thread(s))",
-            "solves_per_s": solves / used}
+            "solves_per_s": solves / used, "seconds": used}
 
 
 def run_reference(args, world, rank):
@@ -432,12 +432,15 @@ def run_reference(args, world, rank):
         if s >= args.warmup:
             per_step.append(cb)
     v = float(np.mean([c["value"] for c in per_step]))
+    ms = float(np.mean([c["seconds"] for c in per_step]) * 1e3)
     line = {
         "impl": "reference", "metric": "rollout-steps/s", "value": v, "unit": "rollout-steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "batched uneven MPPI solves: 256 drones, K logU[1024,16384], N U[20,80], "
-                               "dt 0.02, 5-9 gate courses, objectives 1/3 each", "sample_per_step": per_step[0]["sample"]},
+                               "dt 0.02, 5-9 gate courses, objectives 1/3 each; a step is the oracle's whole "
+                               "solves of the batch's drones in order, up to a time budget",
+                   "sample_per_step": per_step[0]["sample"]},
         "cpu_baseline": {"value": v, "unit": "rollout-steps/s", "cores": per_step[0]["cores"], "kind": "oracle",
                          "sample": per_step[0]["sample"], "host": host_facts()},
         "e2e": {"value": v, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
